@@ -1,0 +1,517 @@
+"""FP64 CPU oracle for the hybrid w-stacking w-projection operator
+Phi = W G C F Z S (arXiv 1903.06555, Sec. 2-3).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's
+CPU-baseline leg may use this package; the product (paper_1903_06555_gb300)
+never imports it and shares no code with it.
+
+The oracle follows the paper's factorisation step by step, in double
+precision, with no blocking, fusion or reordering:
+
+  fold (Sec. 3.3)  ->  k-means w-stacks (Algorithm 1)  ->  per stack k:
+  S~_k (Eq. S~_k: x e^{-2 pi i wbar_k (n-1)} / (g n))  ->  Z (centred zero
+  pad)  ->  F (unnormalised FFT, numpy)  ->  G C_k (Eq. GC_k: one adaptive
+  Gauss-Kronrod integral of Eq. analytic_convolution_hankel per tap)  ->  W.
+
+The adjoint is the exact conjugate transpose of the same steps, summed over
+stacks (Eq. stacked adjoint) and restricted to its real part (the image is
+real, so the fold makes Phi only R-linear).
+
+Readings of points the paper leaves open (kernel normalisation, taper,
+window radius, support rule, tap placement, Algorithm 1 details, quadrature
+acceptance test) are stated where they are used below.
+
+Pins (tests/test_oracle_*.py) check every function against something other
+than itself: closed forms, library routines, an independent 2-D quadrature,
+the direct measurement equation, brute force on tiny inputs, exactness of the
+quadrature rule on polynomials, and adjoint/symmetry identities.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+from fractions import Fraction
+
+import numpy as np
+
+from . import build as _build
+
+_LIB = None
+
+c_double_p = ctypes.POINTER(ctypes.c_double)
+c_int64_p = ctypes.POINTER(ctypes.c_int64)
+c_int32_p = ctypes.POINTER(ctypes.c_int32)
+c_uint8_p = ctypes.POINTER(ctypes.c_uint8)
+
+
+def lib():
+    global _LIB
+    if _LIB is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        d, i64, i32 = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+        for name in ("orc_bessel_j0", "orc_bessel_j1", "orc_bessel_i0", "orc_bessel_i1"):
+            getattr(L, name).restype = d
+            getattr(L, name).argtypes = [d]
+        L.orc_kb.restype = d
+        L.orc_kb.argtypes = [d, d, d]
+        L.orc_taper.restype = d
+        L.orc_taper.argtypes = [d, d, d]
+        L.orc_taper_many.restype = None
+        L.orc_taper_many.argtypes = [c_double_p, i64, d, d, c_double_p]
+        L.orc_chirp.restype = None
+        L.orc_chirp.argtypes = [d, d, d, c_double_p]
+        L.orc_wkernel.restype = None
+        L.orc_wkernel.argtypes = [c_double_p, c_double_p, i64, c_double_p, c_double_p,
+                                  c_double_p, c_int64_p, c_int64_p]
+        L.orc_wkernel_2d.restype = None
+        L.orc_wkernel_2d.argtypes = [c_double_p, c_double_p, c_double_p, i64, c_double_p,
+                                     c_double_p, c_double_p, i32, i32, i32, c_double_p]
+        L.orc_direct.restype = None
+        L.orc_direct.argtypes = [c_double_p, c_double_p, c_double_p, i64, c_double_p, i64,
+                                 c_double_p]
+        for name in ("orc_degrid", "orc_grid"):
+            f = getattr(L, name)
+            f.restype = None
+            f.argtypes = [c_double_p, i64, c_double_p, c_double_p, i64, c_double_p,
+                          c_double_p, c_double_p, c_int32_p, c_double_p, c_uint8_p,
+                          c_double_p, c_int64_p, c_int64_p]
+        L.orc_kmeans.restype = ctypes.c_int
+        L.orc_kmeans.argtypes = [c_double_p, i64, i32, i32, d, c_int32_p, c_double_p]
+        _LIB = L
+    return _LIB
+
+
+def _p(a, t=c_double_p):
+    return a.ctypes.data_as(t)
+
+
+# ----------------------------------------------------------------------------
+# Gauss-Kronrod (7, 15) rule, derived here from its definition
+# ----------------------------------------------------------------------------
+
+def _legendre_power_coeffs(n):
+    """Legendre P_n in the power basis, exact rationals (Bonnet recursion)."""
+    p0, p1 = [Fraction(1)], [Fraction(0), Fraction(1)]
+    if n == 0:
+        return p0
+    for k in range(1, n):
+        # (k+1) P_{k+1} = (2k+1) x P_k - k P_{k-1}
+        nxt = [Fraction(0)] * (k + 2)
+        for i, c in enumerate(p1):
+            nxt[i + 1] += Fraction(2 * k + 1, k + 1) * c
+        for i, c in enumerate(p0):
+            nxt[i] -= Fraction(k, k + 1) * c
+        p0, p1 = p1, nxt
+    return p1
+
+
+_GK = None
+
+
+def gauss_kronrod_15():
+    """(nodes, kronrod weights, gauss weights) on [-1, 1], 15 entries each.
+
+    The 7 Gauss nodes are the zeros of P_7.  The 8 added Kronrod nodes are
+    the zeros of the Stieltjes polynomial E_8, the monic degree-8 polynomial
+    orthogonal to x^k P_7(x) for k = 0..7; by parity E_8 is even and only odd
+    k give conditions.  The 15 Kronrod weights make the rule exact for
+    P_0..P_14.  Exactness up to degree 22 (Kronrod) and 13 (Gauss) is pinned
+    in the tests.
+    """
+    global _GK
+    if _GK is not None:
+        return _GK
+    p7 = _legendre_power_coeffs(7)
+
+    def mom(j):  # integral of P_7(x) x^j over [-1, 1]
+        s = Fraction(0)
+        for i, c in enumerate(p7):
+            d = i + j
+            if d % 2 == 0:
+                s += c * Fraction(2, d + 1)
+        return s
+
+    # E(x) = x^8 + c3 x^6 + c2 x^4 + c1 x^2 + c0, conditions k = 1, 3, 5, 7.
+    rows = [[mom(k + 2 * m) for m in range(4)] for k in (1, 3, 5, 7)]
+    rhs = [-mom(k + 8) for k in (1, 3, 5, 7)]
+    # exact Gaussian elimination over the rationals
+    n = 4
+    A = [r[:] + [b] for r, b in zip(rows, rhs)]
+    for col in range(n):
+        piv = next(r for r in range(col, n) if A[r][col] != 0)
+        A[col], A[piv] = A[piv], A[col]
+        for r in range(n):
+            if r != col and A[r][col] != 0:
+                f = A[r][col] / A[col][col]
+                A[r] = [a - f * b for a, b in zip(A[r], A[col])]
+    c = [A[i][n] / A[i][i] for i in range(n)]
+    quart = [1.0] + [float(c[3]), float(c[2]), float(c[1]), float(c[0])]
+    ys = np.sort(np.real(np.roots(quart)))
+    xs = np.sqrt(ys)
+
+    def e8(x):
+        y = x * x
+        return (((y + float(c[3])) * y + float(c[2])) * y + float(c[1])) * y + float(c[0])
+
+    def de8(x):
+        y = x * x
+        return 2 * x * (((4 * y + 3 * float(c[3])) * y + 2 * float(c[2])) * y + float(c[1]))
+
+    for _ in range(3):  # Newton polish
+        xs = xs - e8(xs) / de8(xs)
+    xg, wg7 = np.polynomial.legendre.leggauss(7)
+    nodes = np.sort(np.concatenate([xg, xs, -xs]))
+    V = np.polynomial.legendre.legvander(nodes, 14).T
+    b = np.zeros(15)
+    b[0] = 2.0
+    wk = np.linalg.solve(V, b)
+    wg = np.zeros(15)
+    for x, w in zip(xg, wg7):
+        wg[np.argmin(np.abs(nodes - x))] = w
+    _GK = (nodes, wk, wg)
+    return _GK
+
+
+def _rule_block():
+    x, wk, wg = gauss_kronrod_15()
+    return np.ascontiguousarray(np.concatenate([x, wk, wg]))
+
+
+# ----------------------------------------------------------------------------
+# Geometry and parameters
+# ----------------------------------------------------------------------------
+
+def beatty_beta(J: float, os_: float) -> float:
+    """Kaiser-Bessel shape from Beatty, Nishimura & Pauly (2005):
+    beta = pi sqrt((J/os)^2 (os - 1/2)^2 - 0.8).  The paper does not name
+    its taper; this reading is the one used throughout."""
+    return math.pi * math.sqrt((J / os_) ** 2 * (os_ - 0.5) ** 2 - 0.8)
+
+
+@dataclass
+class Geometry:
+    """Image and grid geometry.
+
+    Pixels: l_j = (j - N/2) dl, dl = fov/N (uniform in direction cosine;
+    row index = m, column index = l).  Grid: Npad = os N, du = 1/(Npad dl).
+    Kernel radius variable r = du * l (cycles per grid pixel); the window of
+    Eq. analytic_convolution_hankel is r <= R = alpha/2, read with alpha = 1
+    (the disk inscribed in the padded period).  The kernel normalisation is
+    2 pi instead of the paper's 2 pi / du^2: the paper's form is the
+    continuous transform over dl dm, this one matches the unnormalised DFT of
+    the padded image (the two differ by du^2, a scale that the paper's power
+    method normalisation of Phi removes anyway).
+    """
+    N: int
+    os: float
+    fov: float
+    J: float = 4.0
+    beta: float = 0.0
+    alpha: float = 1.0
+    tol_rel: float = 1e-12
+    tol_abs: float = 1e-12
+    max_panels: int = 4000
+
+    def __post_init__(self):
+        self.Npad = int(round(self.os * self.N))
+        if self.Npad % 2 or self.N % 2:
+            raise ValueError("N and os*N must be even")
+        if self.beta == 0.0:
+            self.beta = beatty_beta(self.J, self.os)
+        self.dl = self.fov / self.N
+        self.du = 1.0 / (self.Npad * self.dl)
+        self.R = 0.5 * self.alpha
+        self.l_win = self.R / self.du
+        if self.l_win >= 1.0:
+            raise ValueError("kernel window reaches the horizon")
+        self.n_win = math.sqrt(1.0 - self.l_win ** 2)
+        # Support rule: the chirp exp(-2 pi i dw (n(l)-1)) has local frequency
+        # dw l / n; at the window edge that is dw l_win / (n_win du) grid
+        # pixels, added on both sides of the KB support.
+        self.c_support = self.l_win / (self.n_win * self.du)
+
+    def params(self, tol_rel=None, tol_abs=None):
+        return np.array([self.du, self.R, float(self.J), self.beta,
+                         self.tol_rel if tol_rel is None else tol_rel,
+                         self.tol_abs if tol_abs is None else tol_abs,
+                         float(self.max_panels)], dtype=np.float64)
+
+    def pixel_lm(self):
+        ax = (np.arange(self.N) - self.N // 2) * self.dl
+        l = np.broadcast_to(ax[None, :], (self.N, self.N))
+        m = np.broadcast_to(ax[:, None], (self.N, self.N))
+        return l, m
+
+
+def geometry_from(wl, **kw) -> Geometry:
+    return Geometry(wl.image_n, wl.oversample, math.radians(wl.fov_deg), float(wl.support), **kw)
+
+
+# ----------------------------------------------------------------------------
+# Scalar functions (wrapped C core)
+# ----------------------------------------------------------------------------
+
+def kb(rho, J, beta):
+    return np.vectorize(lib().orc_kb)(rho, float(J), float(beta))
+
+
+def taper(r, J, beta):
+    """g(r): 2-D Fourier transform of the radial KB kernel (closed form)."""
+    r = np.asarray(r, np.float64)
+    flat = np.ascontiguousarray(r.ravel())
+    out = np.zeros(flat.size)
+    lib().orc_taper_many(_p(flat), flat.size, float(J), float(beta), _p(out))
+    return out.reshape(r.shape) if r.shape else float(out[0])
+
+
+def chirp(r, dw, du):
+    out = np.zeros(2)
+    lib().orc_chirp(float(r), float(dw), float(du), _p(out))
+    return complex(out[0], out[1])
+
+
+def wkernel(rho, dw, geo: Geometry, tol_rel=None, tol_abs=None, return_stats=False):
+    """[GC](rho, dw) by adaptive Gauss-Kronrod bisection (one integral per point)."""
+    rho = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, np.float64), np.broadcast(rho, dw).shape)).ravel()
+    dw = np.ascontiguousarray(np.broadcast_to(np.asarray(dw, np.float64), rho.shape)).ravel()
+    out = np.zeros(2 * rho.size)
+    ev = np.zeros(1, np.int64)
+    bad = np.zeros(1, np.int64)
+    lib().orc_wkernel(_p(rho), _p(dw), rho.size, _p(geo.params(tol_rel, tol_abs)),
+                      _p(_rule_block()), _p(out), _p(ev, c_int64_p), _p(bad, c_int64_p))
+    k = out[0::2] + 1j * out[1::2]
+    if return_stats:
+        return k, int(ev[0]), int(bad[0])
+    return k
+
+
+def wkernel_2d(rho_u, rho_v, dw, geo: Geometry, n_gl=20, n_phi=None, n_y=None):
+    """The same kernel as a 2-D integral over the window disk (no Bessel)."""
+    ru = np.ascontiguousarray(np.atleast_1d(np.asarray(rho_u, np.float64)))
+    rv = np.ascontiguousarray(np.broadcast_to(np.asarray(rho_v, np.float64), ru.shape))
+    d = np.ascontiguousarray(np.broadcast_to(np.asarray(dw, np.float64), ru.shape))
+    if n_phi is None or n_y is None:
+        cyc = 2 * geo.R * float(np.max(np.hypot(ru, rv))) + float(np.max(np.abs(d))) * (1 - geo.n_win)
+        n = max(4, int(math.ceil(1.5 * cyc)) + 2)
+        n_phi = n_phi or n
+        n_y = n_y or n
+    x, w = np.polynomial.legendre.leggauss(n_gl)
+    out = np.zeros(2 * ru.size)
+    lib().orc_wkernel_2d(_p(ru), _p(rv), _p(d), ru.size, _p(geo.params()), _p(x), _p(w),
+                         n_gl, n_phi, n_y, _p(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+# ----------------------------------------------------------------------------
+# Direct measurement equation
+# ----------------------------------------------------------------------------
+
+def direct(x, uvw, geo: Geometry):
+    """Eq. meas_eq on the pixel grid (a = 1), summed over non-zero pixels."""
+    l, m = geo.pixel_lm()
+    nz = np.nonzero(x)
+    xv = np.ascontiguousarray(x[nz], dtype=np.float64)
+    lp = np.ascontiguousarray(l[nz], dtype=np.float64)
+    mp = np.ascontiguousarray(m[nz], dtype=np.float64)
+    uvw = np.ascontiguousarray(uvw, dtype=np.float64)
+    y = np.zeros(2 * uvw.shape[0])
+    lib().orc_direct(_p(xv), _p(lp), _p(mp), xv.size, _p(uvw), uvw.shape[0], _p(y))
+    return y[0::2] + 1j * y[1::2]
+
+
+# ----------------------------------------------------------------------------
+# Plan: fold, Algorithm 1, per-visibility support and grid coordinates
+# ----------------------------------------------------------------------------
+
+def fold(uvw):
+    """Sec. 3.3: y*(u, v, -|w|) = y(-u, -v, |w|).  Visibilities with w < 0 are
+    reflected to (-u, -v, -w) and flagged; their model value is conjugated."""
+    uvw = np.array(uvw, dtype=np.float64, copy=True)
+    flag = uvw[:, 2] < 0.0
+    uvw[flag] *= -1.0
+    return uvw, flag
+
+
+def kmeans(w, k, max_iter=100, tol=1e-3):
+    """Algorithm 1 (see orc_kmeans for the reading).  Returns
+    (stack index per visibility, centres, sweeps)."""
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    st = np.zeros(w.size, np.int32)
+    c = np.zeros(k)
+    it = lib().orc_kmeans(_p(w), w.size, int(k), int(max_iter), float(tol), _p(st, c_int32_p), _p(c))
+    return st, c, it
+
+
+@dataclass
+class OraclePlan:
+    geo: Geometry
+    n_stacks: int
+    flag: np.ndarray      # bool, folded visibility
+    stack: np.ndarray     # int32
+    wbar: np.ndarray      # centres
+    dw: np.ndarray        # w - wbar_stack
+    jw: np.ndarray        # int32 support, 0 when dropped
+    upix: np.ndarray      # u / du after folding
+    vpix: np.ndarray
+    weight: np.ndarray
+    dropped: np.ndarray   # bool
+    sweeps: int
+
+
+class SupportError(ValueError):
+    pass
+
+
+SUPPORT_STACK = 0   # one support per stack from its largest |dw| (default)
+SUPPORT_VIS = 1     # one support per visibility from its own |dw|
+
+
+def support(dw, geo: Geometry):
+    """J_w = J + 2 ceil(|dw| c), c = l_win/(n_win du): the KB support widened
+    on both sides by the chirp's bandwidth at the window edge."""
+    return (int(geo.J) + 2 * np.ceil(np.abs(dw) * geo.c_support)).astype(np.int32)
+
+
+def make_plan(uvw, geo: Geometry, n_stacks=1, conj_fold=False, weights=None,
+              kmeans_max_iter=100, kmeans_tol=1e-3, max_support=64,
+              support_rule=SUPPORT_STACK) -> OraclePlan:
+    """Fold, Algorithm 1, grid coordinates u/du, drop visibilities whose own
+    (u, v) lies outside the padded grid [-Npad/2, Npad/2) (their taps would
+    alias; the taps of every kept visibility wrap circularly, G being a
+    circular convolution), then the support: per stack from the largest |dw|
+    of its kept visibilities (SUPPORT_STACK) or per visibility."""
+    uvw = np.asarray(uvw, dtype=np.float64)
+    if conj_fold:
+        uvw, flag = fold(uvw)
+    else:
+        flag = np.zeros(uvw.shape[0], bool)
+    st, c, it = kmeans(uvw[:, 2], n_stacks, kmeans_max_iter, kmeans_tol)
+    dw = uvw[:, 2] - c[st]
+    upix = uvw[:, 0] / geo.du
+    vpix = uvw[:, 1] / geo.du
+    h = geo.Npad // 2
+    dropped = (upix < -h) | (upix >= h) | (vpix < -h) | (vpix >= h)
+    if support_rule == SUPPORT_VIS:
+        jw = support(dw, geo)
+    else:
+        jw = np.zeros(dw.size, np.int32)
+        for k in range(n_stacks):
+            s = (st == k) & ~dropped
+            if s.any():
+                jw[st == k] = support(np.max(np.abs(dw[s])), geo)
+    jw = np.where(dropped, 0, jw).astype(np.int32)
+    if jw.size and int(jw.max()) > max_support:
+        raise SupportError(f"support {int(jw.max())} > {max_support}")
+    wt = np.ones(uvw.shape[0]) if weights is None else np.asarray(weights, np.float64)
+    return OraclePlan(geo, n_stacks, flag, st, c, dw, jw, upix, vpix, wt, dropped, it)
+
+
+# ----------------------------------------------------------------------------
+# Operator
+# ----------------------------------------------------------------------------
+
+def stack_correction(wbar_k, geo: Geometry):
+    """[S~_k]_ii = e^{-2 pi i wbar_k (n_i - 1)} / (g(du |l_i|) n_i) with a_k = 1
+    (Eq. S~_k), on the N x N pixel grid."""
+    l, m = geo.pixel_lm()
+    s = l * l + m * m
+    if np.any(s >= 1.0):
+        raise ValueError("image reaches the horizon")
+    n = np.sqrt(1.0 - s)
+    nm1 = -s / (1.0 + n)
+    g = taper(geo.du * np.sqrt(s), geo.J, geo.beta)
+    return np.exp(-2j * np.pi * wbar_k * nm1) / (g * n)
+
+
+def pad_fft(xs, geo: Geometry):
+    """Z then F: centre the N x N image in Npad x Npad zeros and take the
+    unnormalised DFT Xhat(q) = sum_P X_P e^{-2 pi i q (P - Npad/2)/Npad};
+    frequency q is stored at index q mod Npad."""
+    o = (geo.Npad - geo.N) // 2
+    z = np.zeros((geo.Npad, geo.Npad), np.complex128)
+    z[o:o + geo.N, o:o + geo.N] = xs
+    return np.fft.fft2(np.fft.ifftshift(z))
+
+
+def fft_adjoint_crop(grid, geo: Geometry):
+    """Adjoint of pad_fft: unnormalised inverse DFT, then crop."""
+    z = np.fft.fftshift(np.fft.ifft2(grid)) * (geo.Npad * geo.Npad)
+    o = (geo.Npad - geo.N) // 2
+    return z[o:o + geo.N, o:o + geo.N]
+
+
+def _vis_args(plan: OraclePlan, idx):
+    return (np.ascontiguousarray(plan.upix[idx]), np.ascontiguousarray(plan.vpix[idx]),
+            np.ascontiguousarray(plan.dw[idx]), np.ascontiguousarray(plan.jw[idx], np.int32),
+            np.ascontiguousarray(plan.weight[idx]), np.ascontiguousarray(plan.flag[idx], np.uint8))
+
+
+def degrid(plan: OraclePlan, x, subset=None, tol_rel=None, tol_abs=None, return_stats=False):
+    """y = Phi x (optionally only for the visibilities in `subset`)."""
+    geo = plan.geo
+    M = plan.flag.size
+    sel = np.arange(M) if subset is None else np.asarray(subset)
+    y = np.zeros(sel.size, np.complex128)
+    prm = geo.params(tol_rel, tol_abs)
+    rule = _rule_block()
+    ev_tot = 0
+    bad_tot = 0
+    for k in range(plan.n_stacks):
+        pos = np.nonzero(plan.stack[sel] == k)[0]
+        if pos.size == 0:
+            continue
+        idx = sel[pos]
+        grid = np.ascontiguousarray(pad_fft(x * stack_correction(plan.wbar[k], geo), geo))
+        u, v, d, j, wt, fl = _vis_args(plan, idx)
+        out = np.zeros(2 * idx.size)
+        ev = np.zeros(1, np.int64)
+        bad = np.zeros(1, np.int64)
+        lib().orc_degrid(grid.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, _p(prm),
+                         _p(rule), idx.size, _p(u), _p(v), _p(d), _p(j, c_int32_p), _p(wt),
+                         _p(fl, c_uint8_p), _p(out), _p(ev, c_int64_p), _p(bad, c_int64_p))
+        y[pos] = out[0::2] + 1j * out[1::2]
+        ev_tot += int(ev[0])
+        bad_tot += int(bad[0])
+    if return_stats:
+        return y, ev_tot, bad_tot
+    return y
+
+
+def grid(plan: OraclePlan, y, tol_rel=None, tol_abs=None, return_stats=False):
+    """x = Re(Phi^H y): per stack, grid with the conjugate kernel, inverse
+    unnormalised FFT, crop, multiply by conj(S~_k); summed over stacks."""
+    geo = plan.geo
+    y = np.asarray(y, np.complex128)
+    x = np.zeros((geo.N, geo.N))
+    prm = geo.params(tol_rel, tol_abs)
+    rule = _rule_block()
+    ev_tot = 0
+    bad_tot = 0
+    for k in range(plan.n_stacks):
+        idx = np.nonzero(plan.stack == k)[0]
+        if idx.size == 0:
+            continue
+        g = np.zeros((geo.Npad, geo.Npad), np.complex128)
+        u, v, d, j, wt, fl = _vis_args(plan, idx)
+        yk = np.ascontiguousarray(y[idx])
+        ev = np.zeros(1, np.int64)
+        bad = np.zeros(1, np.int64)
+        lib().orc_grid(g.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, _p(prm),
+                       _p(rule), idx.size, _p(u), _p(v), _p(d), _p(j, c_int32_p), _p(wt),
+                       _p(fl, c_uint8_p), yk.view(np.float64).ctypes.data_as(c_double_p),
+                       _p(ev, c_int64_p), _p(bad, c_int64_p))
+        x += np.real(np.conj(stack_correction(plan.wbar[k], geo)) * fft_adjoint_crop(g, geo))
+        ev_tot += int(ev[0])
+        bad_tot += int(bad[0])
+    if return_stats:
+        return x, ev_tot, bad_tot
+    return x
+
+
+def rel_l2(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    den = np.linalg.norm(b.ravel())
+    return float(np.linalg.norm((a - b).ravel()) / (den if den > 0 else 1.0))
