@@ -1,0 +1,398 @@
+"""Benchmark: w-corrected visibilities/s (degrid + grid) of the GB300
+w-stacking w-projection operator on the MWA-like snapshot workload
+(2048^2 image, 4096^2 grid, FOV 25 deg, 1.95M visibilities, 8 k-means
+w-stacks, conjugate fold, FP32 with FP64 chirp phase, quadrature tol 1e-6).
+
+One step = one y = Phi x (phi_degrid) plus one x = Re(Phi^H y) (phi_grid)
+over every visibility, i.e. every stage of the hot path: per stack S~_k/Z,
+cuFFT, fused w-kernel quadrature + degridding, fused quadrature + gridding,
+inverse cuFFT, crop/chirp/sum.  The plan (fold, Algorithm 1, sort) is built
+once per observation and timed separately; the e2e figure includes it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank runs an
+independent replica of the workload (the operator of one observation does
+not shard across GPUs here) and `value` sums their visibilities over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "w-corrected visibilities/s (degrid+grid) at <=1e-5 rel err vs FP64; p50/p99 latency"
+UNIT = "vis/s"
+FLOPS_PER_TAP_NODE = 36.0     # J0 by a rational/asymptotic approximation (28) + 2 weighted complex MACs (8)
+FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM per clock (Blackwell)
+NUM_SMS = 152
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--support-rule", default="stack", choices=["stack", "vis"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def load_oracle_counts():
+    p = os.path.join(ROOT, "tests", "golden", "mwa_oracle_evals.json")
+    with open(p) as f:
+        return json.load(f)
+
+
+def flush_l2(buf):
+    buf.add_(1.0)   # 256 MiB read-modify-write: larger than the 129 MB L2
+
+
+def workload_inputs(wl):
+    uvw = W.uvw_for(wl)
+    x = W.point_sources(wl.image_n, wl.n_sources, wl.seed)
+    return uvw, x
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+def cpu_oracle_rate(wl, uvw, x, budget_s=20.0, tol=1e-6):
+    """The FP64 oracle, as it stands, on the host cores: degrid + grid of a
+    bounded random sample of the workload's kept visibilities (per-stack
+    grids built before the clock starts), plus one stack's image-domain
+    steps (S~, pad, FFT forward; inverse FFT, crop, S~^H) timed once and
+    charged K times.  Returns (vis/s projected to the full workload,
+    sampled visibilities, measured seconds, threads)."""
+    import oracle as O
+    geo = O.geometry_from(wl, tol_rel=tol, tol_abs=tol)
+    plan = O.make_plan(uvw, geo, wl.n_stacks, wl.conj_fold)
+    kept = np.nonzero(~plan.dropped)[0]
+    order = np.random.default_rng(3).permutation(kept)
+    t0 = time.perf_counter()
+    g0 = O.stack_grids(plan, x, [0])
+    O.image_from_grids(plan, g0)
+    t_image = time.perf_counter() - t0
+    grids = O.stack_grids(plan, x)
+    y = W.random_vis(len(uvw), 9)
+    n_done, t_used, chunk = 0, 0.0, 16
+    vis_budget = max(2.0, budget_s - t_image)
+    while t_used < vis_budget and n_done < len(order):
+        sel = np.sort(order[n_done:n_done + chunk])
+        t0 = time.perf_counter()
+        O.degrid_from_grids(plan, grids, sel)
+        O.grid_to_stacks(plan, y[sel], sel)
+        t_used += time.perf_counter() - t0
+        n_done += sel.size
+        chunk = int(max(16, min(n_done / t_used * (vis_budget - t_used), 4096)))
+    t_full = t_used * (kept.size / n_done) + wl.n_stacks * t_image
+    threads = len(os.sched_getaffinity(0))
+    return kept.size / t_full, n_done, t_used + t_image, threads
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    wl = W.mwa_snapshot()
+    uvw, x = workload_inputs(wl)
+    per_step = []
+    n_tot = 0
+    rates = []
+    for s in range(args.warmup + args.steps):
+        rate, n, t, threads = cpu_oracle_rate(wl, uvw, x, budget_s=8.0)
+        if s >= args.warmup:
+            per_step.append((n, t))
+            rates.append(rate)
+            n_tot = n
+    tot_t = sum(t for _, t in per_step)
+    value = statistics.mean(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(per_step),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "image_n": wl.image_n, "n_stacks": wl.n_stacks,
+                       "quad_tol": 1e-6, "sample_per_step": n_tot},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n_tot} random kept visibilities per step, degrid+grid, "
+                                       "FP64 oracle at quadrature tol 1e-6, plus one stack's "
+                                       "image-domain steps charged per stack; projected to the "
+                                       "full workload"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- our arm
+
+def run_ours(args, ws, rank, local):
+    import paper_1903_06555_gb300 as phi
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = W.mwa_snapshot(seed=0)
+    uvw_np, x_np = workload_inputs(wl)
+    M = len(uvw_np)
+    desc = dict(image_n=wl.image_n, fov_rad=math.radians(wl.fov_deg), oversample=wl.oversample,
+                support=wl.support, n_stacks=wl.n_stacks, conj_fold=int(wl.conj_fold),
+                precision="f32", support_rule=args.support_rule)
+    stream = torch.cuda.current_stream()
+    uvw = torch.from_numpy(uvw_np).to(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plan = phi.Plan(uvw, **desc)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    info = plan.info()
+    n_kept = info["n_kept"]
+    x = torch.from_numpy(x_np).to(dev, torch.float32)
+    y_obs = plan.degrid(x)
+    rms = torch.sqrt(torch.mean(torch.abs(y_obs) ** 2)).item()
+    noise = torch.from_numpy(W.complex_noise(M, 0.01 * rms, 0)).to(dev, torch.complex64)
+    y_obs = y_obs + noise
+    flush = torch.zeros(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+
+    def step():
+        y = plan.degrid(x)
+        d = plan.grid(y_obs)
+        return y, d
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.stats_full(reset=True)
+    plan.timings(reset=True)
+    plan.set_timing(True)
+    times = []
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_id = vis.split(",")[torch.cuda.current_device()] if vis else str(torch.cuda.current_device())
+    with ClockSampler(gpu_id) as clk:
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush_l2(flush)
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    barrier(ws)
+    plan.set_timing(False)
+    times = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    stages = plan.timings(reset=True)
+    bad, taps, tap_nodes = plan.stats_full(reset=True)
+    ms_step = sum(times) / len(times)
+    ms_step_max = max_over_ranks(ms_step, ws)
+    value = ws * n_kept / (ms_step_max / 1e3)
+    lat = sorted(times)
+    p50 = statistics.median(lat)
+    p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
+
+    # roofline: the dominant kernel (fused quadrature + degrid or + grid)
+    counts = load_oracle_counts()
+    evals_per_vis = counts["evals_per_vis_mean"]
+    dom = max(("degrid", "grid"), key=lambda s: stages[s][0])
+    ms_dom, n_dom = stages[dom]
+    launches_per_step = n_dom / args.steps
+    # algorithmic flops of one step's dominant-stage launches = all kept vis
+    flops_step = n_kept * evals_per_vis * FLOPS_PER_TAP_NODE
+    achieved = flops_step / launches_per_step / ((ms_dom / n_dom) / 1e3) / 1e12
+    peaks = measured_peaks()
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_fp32 = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    clocks = clk.summary()
+
+    # end to end through the public API from pinned host buffers
+    e2e = run_e2e(phi, desc, uvw_np, x_np, args.e2e_steps, dev)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl.name, "image_n": wl.image_n, "npad": info["npad"],
+                   "fov_deg": wl.fov_deg, "n_vis": M, "n_kept": n_kept,
+                   "n_dropped": info["n_dropped"], "n_stacks": wl.n_stacks, "conj_fold": wl.conj_fold,
+                   "support": wl.support, "support_rule": args.support_rule,
+                   "jw_per_stack": info["jw"], "quad_tol": 1e-6, "l2": "flushed (256 MiB write) between steps",
+                   "parallelism": f"replicas x{ws}"},
+        "latency_ms": {"p50": p50, "p99": p99, "min": lat[0], "max": lat[-1]},
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in stages.items()},
+        "plan_ms": plan_ms,
+        "kmeans_sweeps": info["kmeans_sweeps"],
+        "quadrature": {"taps_per_step": taps / args.steps, "unconverged_taps": bad,
+                       "gpu_tap_nodes_per_vis": tap_nodes / (2 * args.steps * n_kept),
+                       "oracle_tap_nodes_per_vis_tol1e-6": evals_per_vis},
+        "roofline": {"bound": "alu", "kernel": f"vis_kernel ({dom})", "achieved": achieved,
+                     "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
+                     "traffic": None,
+                     "peak_note": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
+                                  f"{sm_mhz:.0f} MHz (recipe unit counts, max clock)",
+                     "work_note": f"{FLOPS_PER_TAP_NODE:.0f} flops per tap-node x oracle tap-nodes "
+                                  f"per visibility at tol 1e-6"},
+        "e2e": e2e,
+        "gpu_launches": int(4 * sum(1 for c in info["counts"] if c > 0) * args.steps),
+        "clocks": clocks,
+        "wall_s_timed": wall,
+    }
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        rate, n, t, threads = cpu_oracle_rate(wl, uvw_np, x_np, budget_s=20.0)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{n} random kept visibilities of the workload, degrid+grid, "
+                                          f"FP64 oracle at quadrature tol 1e-6, plus one stack's "
+                                          f"image-domain steps charged per stack ({t:.1f} s "
+                                          "measured); projected to the full workload"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def run_e2e(phi, desc, uvw_np, x_np, steps, dev):
+    """Public-API round trip per step: pinned host uvw + image -> device,
+    plan build (fold, Algorithm 1, sort), degrid, grid, results -> host."""
+    uvw_h = torch.from_numpy(uvw_np).pin_memory()
+    x_h = torch.from_numpy(x_np.astype(np.float32)).pin_memory()
+    M = len(uvw_np)
+    y_h = torch.empty(M, dtype=torch.complex64).pin_memory()
+    d_h = torch.empty(x_np.shape, dtype=torch.float32).pin_memory()
+    times = []
+    n_kept = None
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        uvw = uvw_h.to(dev, non_blocking=True)
+        x = x_h.to(dev, non_blocking=True)
+        plan = phi.Plan(uvw, **desc)
+        y = plan.degrid(x)
+        d = plan.grid(y)
+        y_h.copy_(y, non_blocking=True)
+        d_h.copy_(d, non_blocking=True)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        n_kept = plan.info()["n_kept"]
+        plan.close()
+    t = min(times)
+    return {"value": n_kept / t, "unit": UNIT, "seconds": t,
+            "h2d_bytes_per_step": int(uvw_h.numel() * 8 + x_h.numel() * 4),
+            "d2h_bytes_per_step": int(y_h.numel() * 8 + d_h.numel() * 4),
+            "note": "includes plan build (fold, k-means, sort, tables, cuFFT plan)"}
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

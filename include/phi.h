@@ -1,0 +1,214 @@
+/*
+ * phi.h - C ABI of the GB300 w-stacking w-projection measurement operator.
+ *
+ * Operator (Pratley, Johnston-Hollitt & McEwen, arXiv 1903.06555, Sec. 2-3):
+ *
+ *     y = Phi x,      Phi = W G C F Z S                         (Eq. matrix_equation)
+ *     y_k = Phi_k x,  Phi_k = W_k [GC]_k F Z S~_k               (Sec. 3.1)
+ *     x_dirty = [Phi_1^H ... Phi_K^H] [y_1; ...; y_K]          (Eq. stacked adjoint)
+ *
+ * for a real N x N image x and M visibilities y.  Visibilities are split into
+ * K w-stacks by k-means on w (Algorithm 1) after an optional conjugate fold of
+ * negative w onto positive w (Sec. 3.3).  Every w-projection kernel tap
+ *
+ *     [GC](rho, dw) = 2 pi int_0^R g(r) e^{-2 pi i dw (sqrt(1 - r^2/du^2) - 1)}
+ *                              J0(2 pi rho r) r dr          (Eq. analytic_convolution_hankel)
+ *
+ * is computed on the fly by adaptive Gauss-Kronrod quadrature inside the
+ * degridding and gridding kernels; no kernel table and no sparse G is stored.
+ *
+ * Conventions shared by every call:
+ *   - Pixels: l_j = (j - N/2) * dl, dl = fov_rad / N, for row (m) and column
+ *     (l) index j; images are row-major N x N (row = m, column = l).
+ *   - Grid: Npad = oversample * N (even), du = 1 / (Npad * dl) wavelengths.
+ *     Grid frequency q (in [-Npad/2, Npad/2)) is stored at q mod Npad.
+ *   - r = du * l (cycles per grid pixel); the kernel window is r <= R,
+ *     R = alpha / 2.  The kernel is scaled by 2 pi (not the paper's
+ *     2 pi / du^2) so that it matches the unnormalised DFT of the padded image.
+ *   - g is the 2-D Fourier transform of the radial Kaiser-Bessel kernel
+ *     k(rho) = I0(beta sqrt(1 - (2 rho / J)^2)) / I0(beta), |rho| <= J/2.
+ *   - Visibility i of stack k takes the J_w x J_w grid taps q = q0 + (a, b),
+ *     q0 = floor(u_i/du - J_w/2) + 1, wrapping circularly; its model value is
+ *     y_i = W_i sum_taps [GC](|u_i/du - q|, w_i - wbar_k) Xhat_k[q], conjugated
+ *     when the visibility was folded.  Visibilities whose own u/du or v/du lie
+ *     outside [-Npad/2, Npad/2) are dropped: y_i = 0, and they add nothing to
+ *     the adjoint.
+ *   - Quadrature acceptance per tap: sum over panels |K15 - G7| <=
+ *     max(quad_abs_tol, quad_rel_tol * |K|) (paper: 1e-6 relative and absolute,
+ *     Sec. 4).  Taps that do not converge within the refinement cap are
+ *     counted (phi_plan_stats), never an error.
+ *
+ * Memory and streams: every pointer argument named *_dev is a device pointer
+ * owned by the caller; the plan owns everything it allocates (sorted
+ * visibility records, permutation, stack tables, per-pixel factors, one
+ * padded grid, a cuFFT plan and its workspace).  Calls are asynchronous on the
+ * given stream (a cudaStream_t passed as void*; NULL = legacy default stream)
+ * and do not synchronise, except phi_plan_create (it reads the k-means
+ * convergence test back every sweep) and the calls that return host values
+ * (phi_plan_info, phi_plan_stats, phi_wkernel with a non-NULL counter).
+ * A plan may be used by one stream at a time.
+ *
+ * Errors: every call returns PHI_OK (0) or a PHI_ERR_* code; no call traps or
+ * aborts on the device.  phi_error_string() names a code.
+ */
+#ifndef PHI_H_
+#define PHI_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct phi_plan* phi_plan_t;
+
+enum phi_status {
+  PHI_OK = 0,
+  PHI_ERR_ARG = 1,      /* invalid argument or descriptor field              */
+  PHI_ERR_OOM = 2,      /* device allocation failed                          */
+  PHI_ERR_CUDA = 3,     /* a CUDA runtime or cuFFT call failed               */
+  PHI_ERR_HORIZON = 4,  /* image or kernel window reaches l^2 + m^2 >= 1      */
+  PHI_ERR_SUPPORT = 5,  /* a stack needs J_w > max_support (raise K or cap)   */
+  PHI_ERR_TIMEOUT = 6,  /* a bounded wait ran out                            */
+  PHI_ERR_STATE = 7     /* the call does not apply to this plan              */
+};
+
+enum phi_precision {
+  PHI_F32 = 0,  /* FP32 grid, FFT, kernel and accumulation; FP64 chirp phase
+                   argument and FP64 quadrature error accumulation           */
+  PHI_F64 = 1   /* everything in FP64                                        */
+};
+
+enum phi_support_rule {
+  PHI_SUPPORT_STACK = 0,  /* J_w per stack from its largest |w - wbar_k|     */
+  PHI_SUPPORT_VIS = 1     /* J_w per visibility from its own |w - wbar_k|    */
+};
+
+/* Plan descriptor.  phi_plan_desc_default() fills the paper's settings. */
+typedef struct {
+  int32_t image_n;          /* N, even                                       */
+  int32_t support;          /* J, Kaiser-Bessel support in grid pixels, even */
+  int32_t n_stacks;         /* K >= 1 (at most 126)                          */
+  int32_t kmeans_max_iter;  /* Algorithm 1 sweep cap (default 100)           */
+  int32_t conj_fold;        /* 1: fold w < 0 onto w > 0 (Sec. 3.3)           */
+  int32_t max_support;      /* cap on J_w (default 64, at most 256)          */
+  int32_t precision;        /* enum phi_precision                            */
+  int32_t support_rule;     /* enum phi_support_rule                         */
+  int32_t max_refine;       /* panel-count doublings allowed per tap chunk   */
+  int32_t tile;             /* uv tile side used to sort visibilities (32)   */
+  double oversample;        /* os; Npad = os * N must be an even integer     */
+  double fov_rad;           /* full field of view in direction cosine        */
+  double kmeans_tol;        /* Algorithm 1 convergence (default 1e-3)        */
+  double alpha;             /* window radius R = alpha / 2 (default 1)       */
+  double quad_rel_tol;      /* default 1e-6 (Sec. 4)                         */
+  double quad_abs_tol;      /* default 1e-6 (Sec. 4)                         */
+  double kb_beta;           /* 0: pi sqrt((J/os)^2 (os - 1/2)^2 - 0.8)        */
+  double cycles_per_panel;  /* a-priori panel width in integrand cycles (0: auto) */
+} phi_plan_desc;
+
+/* Plan summary filled by phi_plan_info. */
+typedef struct {
+  int64_t n_vis;            /* M as given                                    */
+  int64_t n_kept;           /* M minus dropped visibilities                  */
+  int64_t n_dropped;
+  int64_t device_bytes;     /* device memory held by the plan                */
+  int32_t image_n, npad, n_stacks, kmeans_sweeps, max_jw, precision;
+  double du, dl, beta, window_radius, support_coeff;
+} phi_plan_summary;
+
+/* Fill *desc with the defaults (image size, FOV and stack count are 0 and
+ * must be set by the caller).  Always PHI_OK unless desc is NULL. */
+int phi_plan_desc_default(phi_plan_desc* desc);
+
+/*
+ * Build a plan (Sec. 3.2-3.3 and the per-visibility part of Eq. GC_k):
+ * fold (conj_fold), Algorithm 1 on w, per-stack centres wbar_k, drop test,
+ * support J_w, split u/du into integer base and fraction, sort by
+ * (stack, uv tile), per-pixel image factors, cuFFT plan.
+ *   uvw_dev:     n_vis x 3 float64 (u, v, w in wavelengths), row-major, device.
+ *   weights_dev: n_vis float64 weights W_i (Eq. matrix_equation), or NULL for 1.
+ *   n_vis:       >= 0.
+ * The input buffers are only read during the call.  Returns PHI_ERR_ARG,
+ * PHI_ERR_HORIZON, PHI_ERR_SUPPORT, PHI_ERR_OOM or PHI_ERR_CUDA on failure
+ * (then *out is NULL).  Synchronises `stream`.
+ */
+int phi_plan_create(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
+                    const double* weights_dev, int64_t n_vis, void* stream);
+
+/* Release the plan (after its last call has completed on its stream). */
+void phi_plan_destroy(phi_plan_t plan);
+
+/* Plan summary; per-stack arrays of n_stacks entries are filled when the
+ * pointers are non-NULL: centre wbar_k (Algorithm 1), kept visibility count,
+ * support J_w (per-stack maximum under PHI_SUPPORT_VIS).  Host pointers. */
+int phi_plan_info(phi_plan_t plan, phi_plan_summary* info, double* wbar, int64_t* counts,
+                  int32_t* jw);
+
+/* Quadrature statistics accumulated since plan creation or the last reset:
+ * taps that missed the tolerance at the refinement cap, taps evaluated, and
+ * tap-node integrand evaluations (all refinements included).  Synchronises
+ * `stream`.  reset != 0 zeroes the counters after reading.  NULL outputs are
+ * skipped. */
+int phi_plan_stats(phi_plan_t plan, int64_t* n_unconverged, int64_t* n_taps,
+                   int64_t* n_tap_nodes, int reset, void* stream);
+
+/* Stages of phi_degrid / phi_grid, for per-stage device timing. */
+enum phi_stage {
+  PHI_STAGE_PREP = 0,    /* S~_k and Z                                       */
+  PHI_STAGE_FFT = 1,     /* cuFFT forward or inverse                         */
+  PHI_STAGE_DEGRID = 2,  /* fused w-kernel quadrature + degridding           */
+  PHI_STAGE_GRID = 3,    /* fused w-kernel quadrature + gridding             */
+  PHI_STAGE_FINISH = 4,  /* crop, conj(S~_k), sum over stacks                */
+  PHI_STAGE_CLEAR = 5,   /* zeroing of grid and outputs                      */
+  PHI_NUM_STAGES = 6
+};
+
+/* Enable (1) or disable (0) per-stage timing: CUDA events are recorded on
+ * the call's stream around every stage launch of later phi_degrid/phi_grid
+ * calls.  Timing adds no synchronisation. */
+int phi_plan_set_timing(phi_plan_t plan, int enable);
+
+/* Elapsed device milliseconds and launch counts per stage (arrays of
+ * PHI_NUM_STAGES, host) since the last reset.  Synchronises `stream`. */
+int phi_plan_timings(phi_plan_t plan, double* ms, int64_t* launches, int reset, void* stream);
+
+/*
+ * y = Phi x (Sec. 3.1, Eq. matrix_equation): per stack k, S~_k and Z
+ * (Eq. S~_k, a_k = 1), F (cuFFT, unnormalised forward), then fused
+ * on-the-fly w-kernel quadrature + degridding + W + fold conjugation.
+ *   image_dev: N x N real, float32 (PHI_F32) or float64 (PHI_F64), row-major.
+ *   vis_dev:   n_vis complex (interleaved re, im) float32 / float64, written in
+ *              the caller's visibility order; dropped visibilities get 0.
+ */
+int phi_degrid(phi_plan_t plan, const void* image_dev, void* vis_dev, void* stream);
+
+/*
+ * x = Re(Phi^H y) (Eq. stacked adjoint): per stack k, fused w-kernel
+ * quadrature + gridding of conj([GC]) W y (y conjugated for folded
+ * visibilities), unnormalised inverse FFT (= F^H), crop (Z^T), conj(S~_k),
+ * summed over stacks.  The image is real, so the real part is returned.
+ *   vis_dev:   n_vis complex, caller order (float32 / float64 per precision).
+ *   image_dev: N x N real, overwritten.
+ */
+int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, void* stream);
+
+/*
+ * Evaluate [GC](rho_i, dw_i) (Eq. analytic_convolution_hankel) for n points
+ * with the plan's geometry, taper and quadrature, by the same device routine
+ * the degridder and gridder use.
+ *   rho_dev: n float64 radii in grid pixels (>= 0); dw_dev: n float64 w offsets.
+ *   k_dev:   n complex outputs (float32 or float64 pairs per precision).
+ *   n_unconverged: host pointer or NULL; when non-NULL the call synchronises
+ *   `stream` and stores the number of points that missed the tolerance.
+ */
+int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, int64_t n,
+                void* k_dev, int64_t* n_unconverged, void* stream);
+
+/* Static string naming a status code. */
+const char* phi_error_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHI_H_ */

@@ -448,66 +448,95 @@ def _vis_args(plan: OraclePlan, idx):
             np.ascontiguousarray(plan.weight[idx]), np.ascontiguousarray(plan.flag[idx], np.uint8))
 
 
-def degrid(plan: OraclePlan, x, subset=None, tol_rel=None, tol_abs=None, return_stats=False):
-    """y = Phi x (optionally only for the visibilities in `subset`)."""
+def stack_grids(plan: OraclePlan, x, stacks=None):
+    """F Z S~_k x for every stack k (or the listed ones): {k: Xhat_k}."""
     geo = plan.geo
-    M = plan.flag.size
-    sel = np.arange(M) if subset is None else np.asarray(subset)
-    y = np.zeros(sel.size, np.complex128)
+    ks = range(plan.n_stacks) if stacks is None else stacks
+    return {k: np.ascontiguousarray(pad_fft(x * stack_correction(plan.wbar[k], geo), geo))
+            for k in ks}
+
+
+def degrid_from_grids(plan: OraclePlan, grids, idx, tol_rel=None, tol_abs=None):
+    """W G C_k for the visibilities `idx` (caller order kept), given the
+    stack grids.  Returns (y[idx], integrand evaluations, unconverged taps)."""
+    geo = plan.geo
+    idx = np.asarray(idx)
+    y = np.zeros(idx.size, np.complex128)
     prm = geo.params(tol_rel, tol_abs)
     rule = _rule_block()
-    ev_tot = 0
-    bad_tot = 0
+    ev_tot = bad_tot = 0
     for k in range(plan.n_stacks):
-        pos = np.nonzero(plan.stack[sel] == k)[0]
+        pos = np.nonzero(plan.stack[idx] == k)[0]
         if pos.size == 0:
             continue
-        idx = sel[pos]
-        grid = np.ascontiguousarray(pad_fft(x * stack_correction(plan.wbar[k], geo), geo))
-        u, v, d, j, wt, fl = _vis_args(plan, idx)
-        out = np.zeros(2 * idx.size)
+        sub = idx[pos]
+        g = grids[k]
+        u, v, d, j, wt, fl = _vis_args(plan, sub)
+        out = np.zeros(2 * sub.size)
         ev = np.zeros(1, np.int64)
         bad = np.zeros(1, np.int64)
-        lib().orc_degrid(grid.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, _p(prm),
-                         _p(rule), idx.size, _p(u), _p(v), _p(d), _p(j, c_int32_p), _p(wt),
+        lib().orc_degrid(g.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, _p(prm),
+                         _p(rule), sub.size, _p(u), _p(v), _p(d), _p(j, c_int32_p), _p(wt),
                          _p(fl, c_uint8_p), _p(out), _p(ev, c_int64_p), _p(bad, c_int64_p))
         y[pos] = out[0::2] + 1j * out[1::2]
         ev_tot += int(ev[0])
         bad_tot += int(bad[0])
-    if return_stats:
-        return y, ev_tot, bad_tot
-    return y
+    return y, ev_tot, bad_tot
+
+
+def grid_to_stacks(plan: OraclePlan, y, idx=None, tol_rel=None, tol_abs=None):
+    """(G C_k)^H W for the visibilities `idx` (y indexed like idx): one
+    accumulated grid per stack.  Returns ({k: grid}, evaluations, unconverged)."""
+    geo = plan.geo
+    idx = np.arange(plan.flag.size) if idx is None else np.asarray(idx)
+    y = np.asarray(y, np.complex128)
+    prm = geo.params(tol_rel, tol_abs)
+    rule = _rule_block()
+    grids = {}
+    ev_tot = bad_tot = 0
+    for k in range(plan.n_stacks):
+        pos = np.nonzero(plan.stack[idx] == k)[0]
+        if pos.size == 0:
+            continue
+        sub = idx[pos]
+        g = np.zeros((geo.Npad, geo.Npad), np.complex128)
+        u, v, d, j, wt, fl = _vis_args(plan, sub)
+        yk = np.ascontiguousarray(y[pos])
+        ev = np.zeros(1, np.int64)
+        bad = np.zeros(1, np.int64)
+        lib().orc_grid(g.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, _p(prm),
+                       _p(rule), sub.size, _p(u), _p(v), _p(d), _p(j, c_int32_p), _p(wt),
+                       _p(fl, c_uint8_p), yk.view(np.float64).ctypes.data_as(c_double_p),
+                       _p(ev, c_int64_p), _p(bad, c_int64_p))
+        grids[k] = g
+        ev_tot += int(ev[0])
+        bad_tot += int(bad[0])
+    return grids, ev_tot, bad_tot
+
+
+def image_from_grids(plan: OraclePlan, grids):
+    """sum_k Re(conj(S~_k) Z^T F^H grid_k)."""
+    geo = plan.geo
+    x = np.zeros((geo.N, geo.N))
+    for k, g in grids.items():
+        x += np.real(np.conj(stack_correction(plan.wbar[k], geo)) * fft_adjoint_crop(g, geo))
+    return x
+
+
+def degrid(plan: OraclePlan, x, subset=None, tol_rel=None, tol_abs=None, return_stats=False):
+    """y = Phi x (optionally only for the visibilities in `subset`)."""
+    sel = np.arange(plan.flag.size) if subset is None else np.asarray(subset)
+    grids = stack_grids(plan, x, sorted(set(int(k) for k in plan.stack[sel])))
+    y, ev, bad = degrid_from_grids(plan, grids, sel, tol_rel, tol_abs)
+    return (y, ev, bad) if return_stats else y
 
 
 def grid(plan: OraclePlan, y, tol_rel=None, tol_abs=None, return_stats=False):
     """x = Re(Phi^H y): per stack, grid with the conjugate kernel, inverse
     unnormalised FFT, crop, multiply by conj(S~_k); summed over stacks."""
-    geo = plan.geo
-    y = np.asarray(y, np.complex128)
-    x = np.zeros((geo.N, geo.N))
-    prm = geo.params(tol_rel, tol_abs)
-    rule = _rule_block()
-    ev_tot = 0
-    bad_tot = 0
-    for k in range(plan.n_stacks):
-        idx = np.nonzero(plan.stack == k)[0]
-        if idx.size == 0:
-            continue
-        g = np.zeros((geo.Npad, geo.Npad), np.complex128)
-        u, v, d, j, wt, fl = _vis_args(plan, idx)
-        yk = np.ascontiguousarray(y[idx])
-        ev = np.zeros(1, np.int64)
-        bad = np.zeros(1, np.int64)
-        lib().orc_grid(g.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, _p(prm),
-                       _p(rule), idx.size, _p(u), _p(v), _p(d), _p(j, c_int32_p), _p(wt),
-                       _p(fl, c_uint8_p), yk.view(np.float64).ctypes.data_as(c_double_p),
-                       _p(ev, c_int64_p), _p(bad, c_int64_p))
-        x += np.real(np.conj(stack_correction(plan.wbar[k], geo)) * fft_adjoint_crop(g, geo))
-        ev_tot += int(ev[0])
-        bad_tot += int(bad[0])
-    if return_stats:
-        return x, ev_tot, bad_tot
-    return x
+    grids, ev, bad = grid_to_stacks(plan, y, None, tol_rel, tol_abs)
+    x = image_from_grids(plan, grids)
+    return (x, ev, bad) if return_stats else x
 
 
 def rel_l2(a, b):

@@ -1,0 +1,161 @@
+// Internal declarations of the GB300 w-stacking w-projection library.
+//
+// Layout in HBM (one plan):
+//   VisRec<T>[n_kept]   visibility records sorted by (stack, uv tile), one
+//                       32 B (FP32) or 48 B (FP64) record per visibility:
+//                       fractional grid position, integer base, w offset,
+//                       weight and support;
+//   perm[n_kept]        caller index of each sorted record, bit 31 = folded;
+//   omn_pix[N*N]        1 - n(l, m) per pixel (FP64, for the chirp phase);
+//   corr_pix[N*N]       1 / (g(du |l|) n(l, m)) per pixel (precision T);
+//   node tables         per admissible panel count P: 1 - n(r_j) (FP64) and
+//                       2 pi h g(r_j) r_j (T) at the 15 P Gauss-Kronrod nodes;
+//   grid[Npad*Npad]     one padded complex grid reused by every stack;
+//   counters            work-queue heads and quadrature statistics.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <stdint.h>
+
+#include <utility>
+#include <vector>
+
+#include "../../include/phi.h"
+
+namespace phi {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr float kPiF = 3.14159265358979323846f;
+
+// Admissible panel counts: 1, 2, 3, 4, 6, 8, 12, ... (closed under doubling).
+constexpr int kNumPanelCounts = 16;  // up to 192 panels
+__host__ __device__ inline int panel_count_at(int i) {
+  if (i <= 0) return 1;
+  int e = (i - 1) / 2;
+  return ((i - 1) % 2 == 0 ? 2 : 3) << e;
+}
+__host__ __device__ inline int panel_count_index_for(double want) {
+  int i = 0;
+  while (i < kNumPanelCounts - 1 && panel_count_at(i) < want) ++i;
+  return i;
+}
+__host__ __device__ inline int64_t panel_table_offset(int i) {
+  int64_t off = 0;
+  for (int k = 0; k < i; ++k) off += 15 * panel_count_at(k);
+  return off;
+}
+
+// Panels evaluated per batch out of the per-warp shared node buffer.
+constexpr int kPanelBatch = 32;
+constexpr int kNodeBatch = 15 * kPanelBatch;
+
+template <typename T> struct Cplx;
+template <> struct Cplx<float> { typedef float2 type; };
+template <> struct Cplx<double> { typedef double2 type; };
+
+template <typename T>
+struct __align__(16) VisRec;
+
+template <>
+struct __align__(16) VisRec<float> {
+  float fu, fv;      // u/du - bu, v/du - bv, in [0, 1)
+  int32_t bu, bv;    // floor(u/du), floor(v/du)
+  double dw;         // w - wbar_k (FP64: it multiplies the chirp phase)
+  float weight;      // W_i
+  int32_t jw;        // support J_w (even)
+};
+
+template <>
+struct __align__(16) VisRec<double> {
+  double fu, fv;
+  double dw;
+  double weight;
+  int32_t bu, bv;
+  int32_t jw;
+  int32_t pad;
+};
+
+// Kernel-side constants of one plan.
+struct QuadParams {
+  double R;               // window radius (r units)
+  double du;              // grid spacing (wavelengths)
+  double chirp_coeff;     // local chirp frequency at r = R per unit |dw|
+  double cycles_per_panel;
+  double tol_rel, tol_abs;
+  int max_refine;         // panel-count doublings allowed
+  int npad;
+  const double* node_omn;  // 1 - n(r_j) per node, all panel counts
+  const void* node_hg;     // 2 pi h g(r_j) r_j per node (T)
+};
+
+struct Plan {
+  phi_plan_desc d;
+  int N = 0, npad = 0, K = 0;
+  double dl = 0, du = 0, R = 0, beta = 0, i0beta = 0, l_win = 0, n_win = 0, c_support = 0;
+  double cycles_per_panel = 0;
+  int64_t M = 0, n_kept = 0, n_dropped = 0;
+  int kmeans_sweeps = 0;
+  int max_jw = 0;
+  std::vector<double> wbar;
+  std::vector<int64_t> stack_off;   // K + 1 offsets into the sorted records
+  std::vector<int32_t> stack_jw;    // per-stack support (max under the per-vis rule)
+  // device memory
+  void* recs = nullptr;
+  uint32_t* perm = nullptr;
+  double* omn_pix = nullptr;
+  void* corr_pix = nullptr;
+  double* node_omn = nullptr;
+  void* node_hg = nullptr;
+  void* grid = nullptr;
+  // [0..K) work heads, [K] unconverged taps, [K+1] taps, [K+2] wkernel misses,
+  // [K+3] tap-node evaluations
+  unsigned long long* counters = nullptr;
+  // per-stage timing
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, size_t>> ev_pending;  // (stage, index of start event)
+  double stage_ms[PHI_NUM_STAGES] = {0};
+  int64_t stage_launches[PHI_NUM_STAGES] = {0};
+  cufftHandle fft = 0;
+  bool fft_ok = false;
+  int64_t device_bytes = 0;
+  int num_sms = 0;
+
+  QuadParams quad() const {
+    QuadParams q;
+    q.R = R;
+    q.du = du;
+    q.chirp_coeff = c_support;
+    q.cycles_per_panel = cycles_per_panel;
+    q.tol_rel = d.quad_rel_tol;
+    q.tol_abs = d.quad_abs_tol;
+    q.max_refine = d.max_refine;
+    q.npad = npad;
+    q.node_omn = node_omn;
+    q.node_hg = node_hg;
+    return q;
+  }
+};
+
+#define PHI_CUDA_TRY(expr)                       \
+  do {                                           \
+    cudaError_t e_ = (expr);                     \
+    if (e_ != cudaSuccess) {                     \
+      (void)cudaGetLastError();                  \
+      return e_ == cudaErrorMemoryAllocation ? PHI_ERR_OOM : PHI_ERR_CUDA; \
+    }                                            \
+  } while (0)
+
+// Stage timing (no-ops unless enabled): returns the start-event index or -1.
+long timer_begin(Plan& p, cudaStream_t s);
+void timer_end(Plan& p, long idx, int stage, cudaStream_t s);
+
+// Launchers implemented in phi_ops.cu.
+int launch_node_tables(Plan& p, cudaStream_t s);
+int launch_pixel_tables(Plan& p, cudaStream_t s);
+
+}  // namespace phi
+
+// The opaque handle of the C ABI is the plan itself.
+struct phi_plan : public phi::Plan {};

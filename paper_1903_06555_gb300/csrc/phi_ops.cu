@@ -1,0 +1,684 @@
+// Hot-path kernels of the w-stacking w-projection operator on GB300 (sm_103a):
+//
+//   prep    S~_k and Z (Eq. S~_k): padded grid <- x e^{2 pi i wbar_k (1-n)} / (g n)
+//   F       cuFFT, unnormalised, in place
+//   degrid  fused [GC] quadrature (Eq. analytic_convolution_hankel) + G + W + fold
+//   grid    fused [GC] quadrature + G^H (Eq. stacked adjoint) with float atomics
+//   finish  F^H output -> crop (Z^T) -> conj(S~_k) -> real part -> sum over stacks
+//
+// Kernel evaluation.  One warp owns one visibility.  The chirp part of the
+// integrand, h(r_j) = 2 pi h_p g(r_j) r_j e^{-2 pi i dw (n(r_j) - 1)}, is the
+// same for all J_w^2 taps of the visibility, so the lanes first build it at
+// the Gauss-Kronrod nodes of an a-priori panel partition of [0, R] (FP64
+// phase argument, tabulated 1 - n(r_j) and g(r_j)), then each lane takes one
+// tap and sums J0(2 pi rho r_j) h(r_j) with the Kronrod weights, and the
+// difference against the embedded Gauss rule as the error estimate (summed
+// over panels in FP64).  A chunk of 32 taps whose estimate misses
+// max(abs_tol, rel_tol |K|) is recomputed with twice the panels (up to
+// max_refine times); taps still above tolerance are counted.  The degridder
+// and the gridder run this identical routine, so [GC] and its conjugate
+// transpose pair exactly.
+#include <cuda_runtime.h>
+
+#include "phi_internal.cuh"
+
+namespace phi {
+
+// ---------------------------------------------------------------------------
+// Gauss-Kronrod 7/15 rule on [-1, 1] (published constants of QUADPACK's
+// qk15, Piessens et al. 1983).  Node j = 0..14 runs from -1 to 1.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double gk_abs_node(int i) {
+  return i == 0 ? 0.991455371120812639206854697526329
+       : i == 1 ? 0.949107912342758524526189684047851
+       : i == 2 ? 0.864864423359769072789712788640926
+       : i == 3 ? 0.741531185599394439863864773280788
+       : i == 4 ? 0.586087235467691130294144845693013
+       : i == 5 ? 0.405845151377397166906606412076961
+       : i == 6 ? 0.207784955007898467600689403773245
+                : 0.0;
+}
+__host__ __device__ constexpr double gk_kronrod_weight(int i) {
+  return i == 0 ? 0.022935322010529224963732008058970
+       : i == 1 ? 0.063092092629978553290700663189204
+       : i == 2 ? 0.104790010322250183839876322541518
+       : i == 3 ? 0.140653259715525918745189590510238
+       : i == 4 ? 0.169004726639267902826583426598550
+       : i == 5 ? 0.190350578064785409913256402421014
+       : i == 6 ? 0.204432940075298892414161999234649
+                : 0.209482141084727828012999174891714;
+}
+__host__ __device__ constexpr double gk_gauss_weight(int i) {  // at gk_abs_node(i), odd i
+  return i == 1 ? 0.129484966168869693270611432679082
+       : i == 3 ? 0.279705391489276667901467771423780
+       : i == 5 ? 0.381830050505118944950369775488975
+       : i == 7 ? 0.417959183673469387755102040816327
+                : 0.0;
+}
+__host__ __device__ constexpr int gk_fold(int j) { return j < 7 ? j : 14 - j; }
+__host__ __device__ constexpr double gk_node(int j) {
+  return j < 7 ? -gk_abs_node(j) : gk_abs_node(14 - j);
+}
+__host__ __device__ constexpr double gk_wk(int j) { return gk_kronrod_weight(gk_fold(j)); }
+__host__ __device__ constexpr double gk_wd(int j) {  // Kronrod minus Gauss weight
+  return gk_kronrod_weight(gk_fold(j)) - gk_gauss_weight(gk_fold(j));
+}
+
+// ---------------------------------------------------------------------------
+// Small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float bessel_j0(float x) { return j0f(x); }
+__device__ __forceinline__ double bessel_j0(double x) { return j0(x); }
+__device__ __forceinline__ void sincos_pi(float a, float* s, float* c) { sincospif(a, s, c); }
+__device__ __forceinline__ void sincos_pi(double a, double* s, double* c) { sincospi(a, s, c); }
+
+template <typename C> __device__ __forceinline__ C cmake(double x, double y);
+template <> __device__ __forceinline__ float2 cmake<float2>(double x, double y) {
+  return make_float2(static_cast<float>(x), static_cast<float>(y));
+}
+template <> __device__ __forceinline__ double2 cmake<double2>(double x, double y) {
+  return make_double2(x, y);
+}
+
+__device__ __forceinline__ void atomic_add_c(float2* p, float2 v) { atomicAdd(p, v); }
+__device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
+  atomicAdd(&p->x, v.x);
+  atomicAdd(&p->y, v.y);
+}
+
+__device__ __forceinline__ int64_t pmod64(int64_t a, int64_t n) {
+  int64_t r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// 2-D transform of the radial Kaiser-Bessel kernel (support J = 2a, shape
+// beta): g(r) = 2 pi a^2 I1(z) / (z I0(beta)), z^2 = beta^2 - (2 pi a r)^2,
+// with J1(|z|)/|z| in place of I1(z)/z where z^2 < 0 (Lewitt 1990).
+__device__ double taper_g(double r, double a, double beta, double i0beta) {
+  double q = 2.0 * kPi * a * r;
+  double z2 = beta * beta - q * q;
+  double f;
+  if (fabs(z2) < 1e-12) {
+    f = 0.5 + z2 / 16.0;
+  } else if (z2 > 0.0) {
+    double z = sqrt(z2);
+    f = cyl_bessel_i1(z) / z;
+  } else {
+    double z = sqrt(-z2);
+    f = j1(z) / z;
+  }
+  return 2.0 * kPi * a * a * f / i0beta;
+}
+
+// ---------------------------------------------------------------------------
+// Tables built once per plan
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void node_table_kernel(double R, double du, double a, double beta, double* omn,
+                                  T* hg, int64_t total) {
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= total) return;
+  int i = 0;
+  int64_t off = 0;
+  while (i < kNumPanelCounts - 1 && off + 15 * panel_count_at(i) <= j) {
+    off += 15 * panel_count_at(i);
+    ++i;
+  }
+  int npan = panel_count_at(i);
+  int64_t local = j - off;
+  int p = static_cast<int>(local / 15);
+  int k = static_cast<int>(local % 15);
+  double hw = R / (2.0 * npan);
+  double xk = k < 7 ? -gk_abs_node(k) : gk_abs_node(14 - k);
+  double r = hw * (2.0 * p + 1.0 + xk);
+  double l = r / du;
+  double s = l * l;
+  omn[j] = s / (1.0 + sqrt(1.0 - s));
+  hg[j] = static_cast<T>(2.0 * kPi * hw * taper_g(r, a, beta, cyl_bessel_i0(beta)) * r);
+}
+
+template <typename T>
+__global__ void pixel_table_kernel(int N, double dl, double du, double a, double beta,
+                                   double* omn, T* corr) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)N * N) return;
+  int row = static_cast<int>(idx / N), col = static_cast<int>(idx % N);
+  double l = (col - N / 2) * dl, m = (row - N / 2) * dl;
+  double s = l * l + m * m;
+  double n = sqrt(1.0 - s);
+  omn[idx] = s / (1.0 + n);
+  double g = taper_g(du * sqrt(s), a, beta, cyl_bessel_i0(beta));
+  corr[idx] = static_cast<T>(1.0 / (g * n));
+}
+
+int launch_node_tables(Plan& p, cudaStream_t s) {
+  int64_t total = panel_table_offset(kNumPanelCounts);
+  int blocks = static_cast<int>((total + 255) / 256);
+  double a = 0.5 * p.d.support;
+  if (p.d.precision == PHI_F64)
+    node_table_kernel<double><<<blocks, 256, 0, s>>>(p.R, p.du, a, p.beta, p.node_omn,
+                                                    static_cast<double*>(p.node_hg), total);
+  else
+    node_table_kernel<float><<<blocks, 256, 0, s>>>(p.R, p.du, a, p.beta, p.node_omn,
+                                                   static_cast<float*>(p.node_hg), total);
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
+int launch_pixel_tables(Plan& p, cudaStream_t s) {
+  int64_t total = (int64_t)p.N * p.N;
+  int blocks = static_cast<int>((total + 255) / 256);
+  double a = 0.5 * p.d.support;
+  if (p.d.precision == PHI_F64)
+    pixel_table_kernel<double><<<blocks, 256, 0, s>>>(p.N, p.dl, p.du, a, p.beta, p.omn_pix,
+                                                     static_cast<double*>(p.corr_pix));
+  else
+    pixel_table_kernel<float><<<blocks, 256, 0, s>>>(p.N, p.dl, p.du, a, p.beta, p.omn_pix,
+                                                    static_cast<float*>(p.corr_pix));
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Image-domain steps
+// ---------------------------------------------------------------------------
+
+// S~_k then Z: grid index j (row-major Npad^2) holds padded pixel
+// P = (j + Npad/2) mod Npad (centred image moved to index 0), i.e. image
+// pixel P - (Npad - N)/2, or zero outside the image.
+template <typename T, typename C>
+__global__ void prep_kernel(const T* __restrict__ x, const double* __restrict__ omn,
+                            const T* __restrict__ corr, int N, int npad, double wbar,
+                            C* __restrict__ grid) {
+  int64_t total = (int64_t)npad * npad;
+  int off = (npad - N) / 2;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    int qv = static_cast<int>(j / npad), qu = static_cast<int>(j % npad);
+    int pv = qv + npad / 2;
+    if (pv >= npad) pv -= npad;
+    int pu = qu + npad / 2;
+    if (pu >= npad) pu -= npad;
+    pv -= off;
+    pu -= off;
+    C out = cmake<C>(0.0, 0.0);
+    if (pv >= 0 && pv < N && pu >= 0 && pu < N) {
+      int64_t pix = (int64_t)pv * N + pu;
+      double t = wbar * omn[pix];
+      t -= rint(t);
+      T sn, cs;
+      sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
+      T v = x[pix] * corr[pix];
+      out.x = v * cs;
+      out.y = v * sn;
+    }
+    grid[j] = out;
+  }
+}
+
+// After the inverse FFT: x_p (+)= Re(conj(S~_k) G[P(p)]).
+template <typename T, typename C>
+__global__ void finish_kernel(const C* __restrict__ grid, const double* __restrict__ omn,
+                              const T* __restrict__ corr, int N, int npad, double wbar,
+                              T* __restrict__ x, int accumulate) {
+  int64_t total = (int64_t)N * N;
+  int off = (npad - N) / 2;
+  for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < total;
+       pix += (int64_t)gridDim.x * blockDim.x) {
+    int pv = static_cast<int>(pix / N), pu = static_cast<int>(pix % N);
+    int qv = pv + off + npad / 2;
+    if (qv >= npad) qv -= npad;
+    int qu = pu + off + npad / 2;
+    if (qu >= npad) qu -= npad;
+    C g = grid[(int64_t)qv * npad + qu];
+    double t = wbar * omn[pix];
+    t -= rint(t);
+    T sn, cs;
+    sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
+    T v = corr[pix] * (cs * g.x + sn * g.y);
+    x[pix] = accumulate ? x[pix] + v : v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused kernel quadrature
+// ---------------------------------------------------------------------------
+
+// Build h(r_j) for panels [p0, p0 + np) of the npan-panel partition.
+template <typename T, typename C>
+__device__ __forceinline__ void build_nodes(C* sh, const QuadParams& q, int pidx, int p0, int np,
+                                            double dw, int lane) {
+  const int64_t off = panel_table_offset(pidx) + 15 * (int64_t)p0;
+  const double* omn = q.node_omn + off;
+  const T* hg = static_cast<const T*>(q.node_hg) + off;
+  for (int j = lane; j < 15 * np; j += 32) {
+    double t = dw * omn[j];
+    t -= rint(t);
+    T sn, cs;
+    sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
+    T h = hg[j];
+    C v;
+    v.x = h * cs;
+    v.y = h * sn;
+    sh[j] = v;
+  }
+}
+
+// Sum panels [0, np) held in sh (global panel index p0 + p) for one tap.
+template <typename T, typename C>
+__device__ __forceinline__ void eval_panels(const C* sh, int p0, int np, T B, C& acc,
+                                            double& err) {
+  for (int p = 0; p < np; ++p) {
+    const T a = B * static_cast<T>(2 * (p0 + p) + 1);
+    T kr = 0, ki = 0, dr = 0, di = 0;
+    const C* hp = sh + 15 * p;
+#pragma unroll
+    for (int j = 0; j < 15; ++j) {
+      const T x = fma(B, static_cast<T>(gk_node(j)), a);
+      const T J = bessel_j0(x);
+      const C h = hp[j];
+      const T tr = J * h.x, ti = J * h.y;
+      kr = fma(static_cast<T>(gk_wk(j)), tr, kr);
+      ki = fma(static_cast<T>(gk_wk(j)), ti, ki);
+      dr = fma(static_cast<T>(gk_wd(j)), tr, dr);
+      di = fma(static_cast<T>(gk_wd(j)), ti, di);
+    }
+    acc.x += kr;
+    acc.y += ki;
+    err += static_cast<double>(sqrt(dr * dr + di * di));
+  }
+}
+
+__device__ __forceinline__ int next_panel_index(int pidx) { return pidx == 0 ? 1 : pidx + 2; }
+
+// Evaluate [GC](rho, dw) for one tap per lane (inactive lanes compute a
+// harmless dummy).  pidx and built (the panel-count index whose nodes are
+// resident in sh, or -1) are warp-uniform and updated in place.
+template <typename T, typename C>
+__device__ C eval_chunk(C* sh, const QuadParams& q, T rho, bool active, double dw, int& pidx,
+                        int& built, bool& ok, int lane, unsigned long long& nodes) {
+  int refine = 0;
+  while (true) {
+    const int npan = panel_count_at(pidx);
+    nodes += active ? 15ull * npan : 0ull;
+    const T B = static_cast<T>(2.0 * kPi * (q.R / (2.0 * npan))) * rho;
+    C acc = cmake<C>(0.0, 0.0);
+    double err = 0.0;
+    if (npan <= kPanelBatch) {
+      if (built != pidx) {
+        __syncwarp();
+        build_nodes<T, C>(sh, q, pidx, 0, npan, dw, lane);
+        __syncwarp();
+        built = pidx;
+      }
+      eval_panels<T, C>(sh, 0, npan, B, acc, err);
+    } else {
+      for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
+        const int nb = min(kPanelBatch, npan - p0);
+        __syncwarp();
+        build_nodes<T, C>(sh, q, pidx, p0, nb, dw, lane);
+        __syncwarp();
+        eval_panels<T, C>(sh, p0, nb, B, acc, err);
+      }
+      built = -1;
+    }
+    const double mag = sqrt(static_cast<double>(acc.x) * acc.x + static_cast<double>(acc.y) * acc.y);
+    ok = (!active) || err <= fmax(q.tol_abs, q.tol_rel * mag);
+    const bool any_bad = __any_sync(0xffffffffu, !ok);
+    const int nxt = next_panel_index(pidx);
+    if (!any_bad || refine >= q.max_refine || nxt >= kNumPanelCounts) return acc;
+    ++refine;
+    pidx = nxt;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ int initial_panel_index(const QuadParams& q, T rho_max, double dw) {
+  double cyc = q.R * (static_cast<double>(rho_max) + fabs(dw) * q.chirp_coeff);
+  return panel_count_index_for(cyc / q.cycles_per_panel);
+}
+
+// One warp per visibility, visibilities taken from a work queue.
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256) vis_kernel(const VisRec<T>* __restrict__ recs,
+                                                  const uint32_t* __restrict__ perm, int64_t n,
+                                                  const C* __restrict__ grid_in, C* grid_out,
+                                                  const C* __restrict__ vis_in,
+                                                  C* __restrict__ vis_out, QuadParams q,
+                                                  unsigned long long* head,
+                                                  unsigned long long* stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  C* sh = reinterpret_cast<C*>(smem_raw) + warp * kNodeBatch;
+  unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
+  const int64_t npad = q.npad;
+  while (true) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(head, 1ULL);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= static_cast<unsigned long long>(n)) break;
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw;
+    const int half = Jw / 2;
+    const T fu = r.fu, fv = r.fv;
+    const T mu = fmax(fu + static_cast<T>(half - 1), static_cast<T>(half) - fu);
+    const T mv = fmax(fv + static_cast<T>(half - 1), static_cast<T>(half) - fv);
+    int pidx = initial_panel_index<T>(q, sqrt(mu * mu + mv * mv), r.dw);
+    int built = -1;
+    const uint32_t pm = perm[i];
+    C yv = cmake<C>(0.0, 0.0);
+    if (kGrid) {
+      C v = vis_in[pm & 0x7fffffffu];
+      if (pm >> 31) v.y = -v.y;
+      yv.x = v.x * static_cast<T>(r.weight);
+      yv.y = v.y * static_cast<T>(r.weight);
+    }
+    C accv = cmake<C>(0.0, 0.0);
+    const int ntap = Jw * Jw;
+    for (int t0 = 0; t0 < ntap; t0 += 32) {
+      const int t = t0 + lane;
+      const bool active = t < ntap;
+      const int a = active ? t % Jw : 0;
+      const int b = active ? t / Jw : 0;
+      const int ou = a - half + 1, ov = b - half + 1;
+      const T du_ = fu - static_cast<T>(ou), dv_ = fv - static_cast<T>(ov);
+      const T rho = sqrt(du_ * du_ + dv_ * dv_);
+      bool ok = true;
+      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, pidx, built, ok, lane, my_nodes);
+      if (active) {
+        ++my_taps;
+        if (!ok) ++my_bad;
+        const int64_t gi = pmod64(r.bv + ov, npad) * npad + pmod64(r.bu + ou, npad);
+        if (kGrid) {
+          C add;
+          add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
+          add.y = K.x * yv.y - K.y * yv.x;
+          atomic_add_c(grid_out + gi, add);
+        } else {
+          const C g = grid_in[gi];
+          accv.x += K.x * g.x - K.y * g.y;
+          accv.y += K.x * g.y + K.y * g.x;
+        }
+      }
+    }
+    if (!kGrid) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
+        accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
+      }
+      if (lane == 0) {
+        C out;
+        out.x = accv.x * static_cast<T>(r.weight);
+        out.y = accv.y * static_cast<T>(r.weight);
+        if (pm >> 31) out.y = -out.y;
+        vis_out[pm & 0x7fffffffu] = out;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
+    my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
+    my_nodes += __shfl_xor_sync(0xffffffffu, my_nodes, o);
+  }
+  if (lane == 0 && my_taps) {
+    atomicAdd(stats, my_bad);
+    atomicAdd(stats + 1, my_taps);
+    atomicAdd(stats + 3, my_nodes);
+  }
+}
+
+// phi_wkernel: one warp per point, lane 0 carries the tap.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__ rho_in,
+                                                      const double* __restrict__ dw_in, int64_t n,
+                                                      C* __restrict__ out, QuadParams q,
+                                                      unsigned long long* bad) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  C* sh = reinterpret_cast<C*>(smem_raw) + warp * kNodeBatch;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t i = blockIdx.x * wpb + warp; i < n; i += (int64_t)gridDim.x * wpb) {
+    const T rho = static_cast<T>(rho_in[i]);
+    const double dw = dw_in[i];
+    int pidx = initial_panel_index<T>(q, rho, dw);
+    int built = -1;
+    bool ok = true;
+    unsigned long long nodes = 0;
+    const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw, pidx, built, ok, lane, nodes);
+    if (lane == 0) {
+      out[i] = K;
+      if (!ok) atomicAdd(bad, 1ULL);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side of the operator
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kVisThreads = 256;
+
+template <typename T, typename C>
+int blocks_for_vis(const Plan& p, size_t smem) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vis_kernel<T, C, false>,
+                                                    kVisThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  return per_sm * p.num_sms;
+}
+
+template <typename T, typename C>
+int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
+  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(C);
+  long ev = timer_begin(p, s);
+  PHI_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(C) * (size_t)p.M, s));
+  PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
+  timer_end(p, ev, PHI_STAGE_CLEAR, s);
+  const int vis_blocks = blocks_for_vis<T, C>(p, smem);
+  const int img_blocks = p.num_sms * 8;
+  const QuadParams q = p.quad();
+  C* grid = static_cast<C*>(p.grid);
+  for (int k = 0; k < p.K; ++k) {
+    const int64_t b0 = p.stack_off[k], nk = p.stack_off[k + 1] - b0;
+    if (nk == 0) continue;
+    ev = timer_begin(p, s);
+    prep_kernel<T, C><<<img_blocks, 256, 0, s>>>(x, p.omn_pix, static_cast<const T*>(p.corr_pix),
+                                                 p.N, p.npad, p.wbar[k], grid);
+    PHI_CUDA_TRY(cudaGetLastError());
+    timer_end(p, ev, PHI_STAGE_PREP, s);
+    ev = timer_begin(p, s);
+    if (cufftSetStream(p.fft, s) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    cufftResult fr;
+    if (sizeof(T) == 8)
+      fr = cufftExecZ2Z(p.fft, reinterpret_cast<cufftDoubleComplex*>(grid),
+                        reinterpret_cast<cufftDoubleComplex*>(grid), CUFFT_FORWARD);
+    else
+      fr = cufftExecC2C(p.fft, reinterpret_cast<cufftComplex*>(grid),
+                        reinterpret_cast<cufftComplex*>(grid), CUFFT_FORWARD);
+    if (fr != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    timer_end(p, ev, PHI_STAGE_FFT, s);
+    ev = timer_begin(p, s);
+    vis_kernel<T, C, false><<<vis_blocks, kVisThreads, smem, s>>>(
+        static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y, q,
+        p.counters + k, p.counters + p.K);
+    PHI_CUDA_TRY(cudaGetLastError());
+    timer_end(p, ev, PHI_STAGE_DEGRID, s);
+  }
+  return PHI_OK;
+}
+
+template <typename T, typename C>
+int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
+  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(C);
+  PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
+  const int vis_blocks = blocks_for_vis<T, C>(p, smem);
+  const int img_blocks = p.num_sms * 8;
+  const QuadParams q = p.quad();
+  C* grid = static_cast<C*>(p.grid);
+  bool first = true;
+  for (int k = 0; k < p.K; ++k) {
+    const int64_t b0 = p.stack_off[k], nk = p.stack_off[k + 1] - b0;
+    if (nk == 0) continue;
+    long ev = timer_begin(p, s);
+    PHI_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * (size_t)p.npad * p.npad, s));
+    timer_end(p, ev, PHI_STAGE_CLEAR, s);
+    ev = timer_begin(p, s);
+    vis_kernel<T, C, true><<<vis_blocks, kVisThreads, smem, s>>>(
+        static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr, q,
+        p.counters + k, p.counters + p.K);
+    PHI_CUDA_TRY(cudaGetLastError());
+    timer_end(p, ev, PHI_STAGE_GRID, s);
+    ev = timer_begin(p, s);
+    if (cufftSetStream(p.fft, s) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    cufftResult fr;
+    if (sizeof(T) == 8)
+      fr = cufftExecZ2Z(p.fft, reinterpret_cast<cufftDoubleComplex*>(grid),
+                        reinterpret_cast<cufftDoubleComplex*>(grid), CUFFT_INVERSE);
+    else
+      fr = cufftExecC2C(p.fft, reinterpret_cast<cufftComplex*>(grid),
+                        reinterpret_cast<cufftComplex*>(grid), CUFFT_INVERSE);
+    if (fr != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    timer_end(p, ev, PHI_STAGE_FFT, s);
+    ev = timer_begin(p, s);
+    finish_kernel<T, C><<<img_blocks, 256, 0, s>>>(grid, p.omn_pix,
+                                                   static_cast<const T*>(p.corr_pix), p.N, p.npad,
+                                                   p.wbar[k], x, first ? 0 : 1);
+    PHI_CUDA_TRY(cudaGetLastError());
+    timer_end(p, ev, PHI_STAGE_FINISH, s);
+    first = false;
+  }
+  if (first) PHI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)p.N * p.N, s));
+  return PHI_OK;
+}
+
+template <typename T, typename C>
+int run_wkernel(Plan& p, const double* rho, const double* dw, int64_t n, C* out,
+                int64_t* n_bad, cudaStream_t s) {
+  unsigned long long* bad = p.counters + p.K + 2;
+  PHI_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+  if (n > 0) {
+    const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(C);
+    int64_t want = (n + 7) / 8;
+    int blocks = static_cast<int>(want < 65535 ? want : 65535);
+    wkernel_kernel<T, C><<<blocks, kVisThreads, smem, s>>>(rho, dw, n, out, p.quad(), bad);
+    PHI_CUDA_TRY(cudaGetLastError());
+  }
+  if (n_bad) {
+    unsigned long long h = 0;
+    PHI_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_bad = static_cast<int64_t>(h);
+  }
+  return PHI_OK;
+}
+
+}  // namespace
+
+long timer_begin(Plan& p, cudaStream_t s) {
+  if (!p.timing) return -1;
+  size_t idx = 2 * p.ev_pending.size();
+  while (p.ev_pool.size() < idx + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    p.ev_pool.push_back(e);
+  }
+  if (cudaEventRecord(p.ev_pool[idx], s) != cudaSuccess) return -1;
+  return static_cast<long>(idx);
+}
+
+void timer_end(Plan& p, long idx, int stage, cudaStream_t s) {
+  if (idx < 0) return;
+  if (cudaEventRecord(p.ev_pool[idx + 1], s) != cudaSuccess) return;
+  p.ev_pending.emplace_back(stage, static_cast<size_t>(idx));
+}
+
+int set_kernel_smem_limits() {
+  const size_t f32 = (kVisThreads / 32) * kNodeBatch * sizeof(float2);
+  const size_t f64 = (kVisThreads / 32) * kNodeBatch * sizeof(double2);
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<float, float2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<float, float2, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(wkernel_kernel<float, float2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<double, double2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<double, double2, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(wkernel_kernel<double, double2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
+  return PHI_OK;
+}
+
+}  // namespace phi
+
+extern "C" int phi_degrid(phi_plan_t plan, const void* image_dev, void* vis_dev, void* stream) {
+  if (!plan || (!image_dev && plan->M > 0) || (!vis_dev && plan->M > 0)) return PHI_ERR_ARG;
+  phi::Plan& p = *plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.M == 0) return PHI_OK;
+  if (p.d.precision == PHI_F64)
+    return phi::run_degrid<double, double2>(p, static_cast<const double*>(image_dev),
+                                            static_cast<double2*>(vis_dev), s);
+  return phi::run_degrid<float, float2>(p, static_cast<const float*>(image_dev),
+                                        static_cast<float2*>(vis_dev), s);
+}
+
+extern "C" int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, void* stream) {
+  if (!plan || !image_dev || (!vis_dev && plan->M > 0)) return PHI_ERR_ARG;
+  phi::Plan& p = *plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.d.precision == PHI_F64)
+    return phi::run_grid<double, double2>(p, static_cast<const double2*>(vis_dev),
+                                          static_cast<double*>(image_dev), s);
+  return phi::run_grid<float, float2>(p, static_cast<const float2*>(vis_dev),
+                                      static_cast<float*>(image_dev), s);
+}
+
+extern "C" int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, int64_t n,
+                           void* k_dev, int64_t* n_unconverged, void* stream) {
+  if (!plan || n < 0 || (n > 0 && (!rho_dev || !dw_dev || !k_dev))) return PHI_ERR_ARG;
+  phi::Plan& p = *plan;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.d.precision == PHI_F64)
+    return phi::run_wkernel<double, double2>(p, rho_dev, dw_dev, n, static_cast<double2*>(k_dev),
+                                             n_unconverged, s);
+  return phi::run_wkernel<float, float2>(p, rho_dev, dw_dev, n, static_cast<float2*>(k_dev),
+                                         n_unconverged, s);
+}
+
+extern "C" int phi_plan_set_timing(phi_plan_t plan, int enable) {
+  if (!plan) return PHI_ERR_ARG;
+  plan->timing = enable != 0;
+  return PHI_OK;
+}
+
+extern "C" int phi_plan_timings(phi_plan_t plan, double* ms, int64_t* launches, int reset,
+                                void* stream) {
+  if (!plan) return PHI_ERR_ARG;
+  phi::Plan& p = *plan;
+  PHI_CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+  for (const auto& pr : p.ev_pending) {
+    float t = 0.f;
+    PHI_CUDA_TRY(cudaEventSynchronize(p.ev_pool[pr.second + 1]));
+    PHI_CUDA_TRY(cudaEventElapsedTime(&t, p.ev_pool[pr.second], p.ev_pool[pr.second + 1]));
+    p.stage_ms[pr.first] += t;
+    p.stage_launches[pr.first] += 1;
+  }
+  p.ev_pending.clear();
+  for (int i = 0; i < PHI_NUM_STAGES; ++i) {
+    if (ms) ms[i] = p.stage_ms[i];
+    if (launches) launches[i] = p.stage_launches[i];
+    if (reset) {
+      p.stage_ms[i] = 0.0;
+      p.stage_launches[i] = 0;
+    }
+  }
+  return PHI_OK;
+}

@@ -1,0 +1,599 @@
+// Plan construction for the GB300 w-stacking w-projection operator:
+// conjugate fold (Sec. 3.3), k-means w-stacking (Algorithm 1), per-stack
+// centres, drop test, support J_w, split of u/du into an integer base and a
+// fraction, sort by (stack, uv tile), per-pixel and per-node tables, cuFFT.
+//
+// All per-visibility work runs on the device.  The k-means sums are formed
+// deterministically (fixed block ranges, warp butterflies, fixed-order
+// combination), so a plan is bit-reproducible run to run.
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "phi_internal.cuh"
+
+namespace phi {
+
+int set_kernel_smem_limits();
+
+namespace {
+
+constexpr int kPlanThreads = 256;
+
+// Fold and extract w.  flag = 1 when the visibility was reflected.
+__global__ void fold_kernel(const double* __restrict__ uvw, int64_t M, int fold,
+                            double* __restrict__ w_out, uint8_t* __restrict__ flag,
+                            double* __restrict__ part_min, double* __restrict__ part_max) {
+  __shared__ double smin[kPlanThreads], smax[kPlanThreads];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double w = uvw[3 * i + 2];
+    uint8_t f = (fold && w < 0.0) ? 1 : 0;
+    if (f) w = -w;
+    w_out[i] = w;
+    flag[i] = f;
+    lo = fmin(lo, w);
+    hi = fmax(hi, w);
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part_min[blockIdx.x] = smin[0];
+    part_max[blockIdx.x] = smax[0];
+  }
+}
+
+// One sweep of Algorithm 1: nearest centre by (wbar_q - w_p)^2 (strict <, so
+// the lowest index wins ties) and per-block partial sums and counts per stack.
+// Block b owns the contiguous range [b*chunk, (b+1)*chunk); inside it each
+// warp takes 32 consecutive visibilities at a time and reduces every stack
+// present among them with a butterfly (lane 0's fixed order).
+__global__ void kmeans_sweep_kernel(const double* __restrict__ w, int64_t M, int64_t chunk,
+                                    const double* __restrict__ centres, int K,
+                                    int32_t* __restrict__ stack, double* __restrict__ part_sum,
+                                    double* __restrict__ part_cnt) {
+  extern __shared__ double sm[];
+  const int nwarps = blockDim.x >> 5;
+  double* c = sm;
+  double* wsum = sm + K;
+  double* wcnt = wsum + nwarps * K;
+  for (int q = threadIdx.x; q < K; q += blockDim.x) c[q] = centres[q];
+  for (int q = threadIdx.x; q < nwarps * K; q += blockDim.x) {
+    wsum[q] = 0.0;
+    wcnt[q] = 0.0;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t b0 = blockIdx.x * chunk;
+  const int64_t b1 = min(M, b0 + chunk);
+  for (int64_t base = b0 + 32 * (int64_t)warp; base < b1; base += 32 * (int64_t)nwarps) {
+    const int64_t i = base + lane;
+    const bool valid = i < b1;
+    double wi = 0.0;
+    int s = 0;  // also the stack of a non-finite w (every comparison fails)
+    if (valid) {
+      wi = w[i];
+      double best = INFINITY;
+      for (int q = 0; q < K; ++q) {
+        const double d = (c[q] - wi) * (c[q] - wi);
+        if (d < best) {
+          best = d;
+          s = q;
+        }
+      }
+      stack[i] = s;
+    }
+    unsigned rem = __ballot_sync(0xffffffffu, valid);
+    while (rem) {
+      const int leader = __ffs(rem) - 1;
+      const int sq = __shfl_sync(0xffffffffu, s, leader);
+      const unsigned mem = __ballot_sync(0xffffffffu, valid && s == sq);
+      double v = ((mem >> lane) & 1u) ? wi : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        wsum[warp * K + sq] += v;
+        wcnt[warp * K + sq] += static_cast<double>(__popc(mem));
+      }
+      rem &= ~mem;
+    }
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < K; q += blockDim.x) {
+    double s = 0.0, n = 0.0;
+    for (int wp = 0; wp < nwarps; ++wp) {
+      s += wsum[wp * K + q];
+      n += wcnt[wp * K + q];
+    }
+    part_sum[(int64_t)blockIdx.x * K + q] = s;
+    part_cnt[(int64_t)blockIdx.x * K + q] = n;
+  }
+}
+
+// Centre update: wbar_q = sum / count, or 0 for an empty stack (Algorithm 1),
+// and the convergence measure mean_q |new - old| / max(|old|, eps).
+// out[0..K) new centres, out[K..2K) counts, out[2K] measure.
+__global__ void kmeans_update_kernel(const double* __restrict__ part_sum,
+                                     const double* __restrict__ part_cnt, int nblocks, int K,
+                                     double eps, double* __restrict__ centres,
+                                     double* __restrict__ out) {
+  __shared__ double rel[128];
+  const int q = threadIdx.x;
+  if (q < K) {
+    double s = 0.0, n = 0.0;
+    for (int b = 0; b < nblocks; ++b) {
+      s += part_sum[(int64_t)b * K + q];
+      n += part_cnt[(int64_t)b * K + q];
+    }
+    const double old = centres[q];
+    const double nc = n > 0.0 ? s / n : 0.0;
+    rel[q] = fabs(nc - old) / fmax(fabs(old), eps);
+    centres[q] = nc;
+    out[q] = nc;
+    out[K + q] = n;
+  }
+  __syncthreads();
+  if (q == 0) {
+    double d = 0.0;
+    for (int k = 0; k < K; ++k) d += rel[k];
+    out[2 * K] = d / K;
+  }
+}
+
+// Per visibility after clustering: w offset, drop test, sort key, and the
+// per-stack largest |dw| and kept count (order-independent atomics: integer
+// adds and max on the bit pattern of non-negative doubles).
+__global__ void classify_kernel(const double* __restrict__ uvw, const uint8_t* __restrict__ flag,
+                                const double* __restrict__ w_fold,
+                                const int32_t* __restrict__ stack,
+                                const double* __restrict__ centres, int64_t M, int K, double du,
+                                int npad, int tile, int tiles_per_row,
+                                uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                unsigned long long* __restrict__ maxabs_bits,
+                                unsigned long long* __restrict__ kept) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double sgn = flag[i] ? -1.0 : 1.0;
+    const double up = sgn * uvw[3 * i] / du;
+    const double vp = sgn * uvw[3 * i + 1] / du;
+    const int s = stack[i];
+    const double h = 0.5 * npad;
+    const bool drop = !(up >= -h && up < h && vp >= -h && vp < h);
+    uint32_t key;
+    if (drop) {
+      key = static_cast<uint32_t>(K) << 24;
+    } else {
+      const int64_t bu = static_cast<int64_t>(floor(up)) + npad / 2;
+      const int64_t bv = static_cast<int64_t>(floor(vp)) + npad / 2;
+      const uint32_t tu = static_cast<uint32_t>(bu / tile), tv = static_cast<uint32_t>(bv / tile);
+      key = (static_cast<uint32_t>(s) << 24) | (tv * tiles_per_row + tu);
+      const double a = fabs(w_fold[i] - centres[s]);
+      atomicMax(maxabs_bits + s, static_cast<unsigned long long>(__double_as_longlong(a)));
+      atomicAdd(kept + s, 1ULL);
+    }
+    keys[i] = key;
+    vals[i] = static_cast<uint32_t>(i);
+  }
+}
+
+template <typename T>
+__global__ void records_kernel(const double* __restrict__ uvw, const uint8_t* __restrict__ flag,
+                               const double* __restrict__ w_fold,
+                               const int32_t* __restrict__ stack,
+                               const double* __restrict__ centres,
+                               const double* __restrict__ weights,
+                               const uint32_t* __restrict__ sorted_vals, int64_t n_kept,
+                               double du, int J, double c_support, int per_vis,
+                               const int32_t* __restrict__ stack_jw, VisRec<T>* __restrict__ recs,
+                               uint32_t* __restrict__ perm) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_kept;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t o = sorted_vals[i];
+    const double sgn = flag[o] ? -1.0 : 1.0;
+    const double up = sgn * uvw[3 * (int64_t)o] / du;
+    const double vp = sgn * uvw[3 * (int64_t)o + 1] / du;
+    const int s = stack[o];
+    const double dw = w_fold[o] - centres[s];
+    const double bu = floor(up), bv = floor(vp);
+    VisRec<T> r;
+    r.fu = static_cast<T>(up - bu);
+    r.fv = static_cast<T>(vp - bv);
+    r.bu = static_cast<int32_t>(bu);
+    r.bv = static_cast<int32_t>(bv);
+    r.dw = dw;
+    r.weight = static_cast<T>(weights ? weights[o] : 1.0);
+    r.jw = per_vis ? J + 2 * static_cast<int32_t>(ceil(fabs(dw) * c_support)) : stack_jw[s];
+    recs[i] = r;
+    perm[i] = o | (flag[o] ? 0x80000000u : 0u);
+  }
+}
+
+struct Scratch {
+  std::vector<void*> ptrs;
+  ~Scratch() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename X>
+  cudaError_t alloc(X** p, size_t count) {
+    void* raw = nullptr;
+    cudaError_t e = cudaMalloc(&raw, std::max<size_t>(count, 1) * sizeof(X));
+    if (e == cudaSuccess) {
+      ptrs.push_back(raw);
+      *p = static_cast<X*>(raw);
+    }
+    return e;
+  }
+};
+
+void free_plan(Plan* p) {
+  if (!p) return;
+  if (p->fft_ok) cufftDestroy(p->fft);
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  cudaFree(p->recs);
+  cudaFree(p->perm);
+  cudaFree(p->omn_pix);
+  cudaFree(p->corr_pix);
+  cudaFree(p->node_omn);
+  cudaFree(p->node_hg);
+  cudaFree(p->grid);
+  cudaFree(p->counters);
+}
+
+template <typename X>
+cudaError_t owned_alloc(Plan& p, X** ptr, size_t count) {
+  void* raw = nullptr;
+  size_t bytes = std::max<size_t>(count, 1) * sizeof(X);
+  cudaError_t e = cudaMalloc(&raw, bytes);
+  if (e == cudaSuccess) {
+    *ptr = static_cast<X*>(raw);
+    p.device_bytes += static_cast<int64_t>(bytes);
+  }
+  return e;
+}
+
+#define PHI_TRY(expr)             \
+  do {                            \
+    int st_ = (expr);             \
+    if (st_ != PHI_OK) return st_; \
+  } while (0)
+
+int validate(const phi_plan_desc& d, int64_t M) {
+  if (M < 0 || M > 0x7fffffffLL) return PHI_ERR_ARG;
+  if (d.image_n < 2 || d.image_n % 2) return PHI_ERR_ARG;
+  if (!(d.oversample >= 1.0) || !(d.fov_rad > 0.0)) return PHI_ERR_ARG;
+  double np = d.oversample * d.image_n;
+  if (std::fabs(np - std::round(np)) > 1e-9 || static_cast<int64_t>(std::round(np)) % 2)
+    return PHI_ERR_ARG;
+  if (std::round(np) > 65536) return PHI_ERR_ARG;
+  if (d.support < 2 || d.support % 2 || d.support > 64) return PHI_ERR_ARG;
+  if (d.n_stacks < 1 || d.n_stacks > 126) return PHI_ERR_ARG;
+  if (d.kmeans_max_iter < 1 || !(d.kmeans_tol >= 0.0)) return PHI_ERR_ARG;
+  if (d.max_support < d.support || d.max_support > 256) return PHI_ERR_ARG;
+  if (d.precision != PHI_F32 && d.precision != PHI_F64) return PHI_ERR_ARG;
+  if (d.support_rule != PHI_SUPPORT_STACK && d.support_rule != PHI_SUPPORT_VIS) return PHI_ERR_ARG;
+  if (!(d.alpha > 0.0) || !(d.quad_rel_tol > 0.0) || !(d.quad_abs_tol > 0.0)) return PHI_ERR_ARG;
+  if (d.max_refine < 0 || d.max_refine > 8) return PHI_ERR_ARG;
+  if (d.tile < 0 || d.tile > 4096) return PHI_ERR_ARG;
+  if (d.kb_beta < 0.0 || d.cycles_per_panel < 0.0) return PHI_ERR_ARG;
+  return PHI_OK;
+}
+
+int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStream_t s) {
+  const phi_plan_desc& d = p.d;
+  p.N = d.image_n;
+  p.npad = static_cast<int>(std::lround(d.oversample * d.image_n));
+  p.K = d.n_stacks;
+  p.M = M;
+  p.dl = d.fov_rad / p.N;
+  p.du = 1.0 / (p.npad * p.dl);
+  p.R = 0.5 * d.alpha;
+  p.beta = d.kb_beta > 0.0
+               ? d.kb_beta
+               : kPi * std::sqrt((double(d.support) / d.oversample) *
+                                     (double(d.support) / d.oversample) *
+                                     (d.oversample - 0.5) * (d.oversample - 0.5) -
+                                 0.8);
+  if (!(p.beta > 0.0)) return PHI_ERR_ARG;
+  p.l_win = p.R / p.du;
+  // Image corner and kernel window must stay below the horizon, and the
+  // window must cover the image corners.
+  const double half_fov = 0.5 * p.N * p.dl;
+  if (p.l_win >= 1.0 || 2.0 * half_fov * half_fov >= 1.0) return PHI_ERR_HORIZON;
+  if (std::sqrt(2.0) * half_fov > p.l_win) return PHI_ERR_ARG;
+  p.n_win = std::sqrt(1.0 - p.l_win * p.l_win);
+  p.c_support = p.l_win / (p.n_win * p.du);
+  const double tol = std::min(d.quad_rel_tol, d.quad_abs_tol);
+  p.cycles_per_panel = d.cycles_per_panel > 0.0
+                           ? d.cycles_per_panel
+                           : std::min(2.0, std::max(0.25, 1.5 * std::pow(tol / 1e-6, 1.0 / 14.0)));
+
+  int dev = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, dev));
+  PHI_TRY(set_kernel_smem_limits());
+
+  const int K = p.K;
+  p.wbar.assign(K, 0.0);
+  p.stack_off.assign(K + 1, 0);
+  p.stack_jw.assign(K, 0);
+  PHI_CUDA_TRY(owned_alloc(p, &p.counters, static_cast<size_t>(K) + 4));
+  PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * (K + 4), s));
+
+  Scratch tmp;
+  const int nblk = std::max(1, std::min<int>(p.num_sms * 4,
+                                             static_cast<int>((M + kPlanThreads - 1) / kPlanThreads)));
+  double *w_fold = nullptr, *pmin = nullptr, *pmax = nullptr, *centres = nullptr,
+         *psum = nullptr, *pcnt = nullptr, *upd = nullptr;
+  uint8_t* flag = nullptr;
+  int32_t* stack = nullptr;
+  PHI_CUDA_TRY(tmp.alloc(&w_fold, M));
+  PHI_CUDA_TRY(tmp.alloc(&flag, M));
+  PHI_CUDA_TRY(tmp.alloc(&stack, M));
+  PHI_CUDA_TRY(tmp.alloc(&pmin, nblk));
+  PHI_CUDA_TRY(tmp.alloc(&pmax, nblk));
+  PHI_CUDA_TRY(tmp.alloc(&centres, K));
+  PHI_CUDA_TRY(tmp.alloc(&psum, static_cast<size_t>(nblk) * K));
+  PHI_CUDA_TRY(tmp.alloc(&pcnt, static_cast<size_t>(nblk) * K));
+  PHI_CUDA_TRY(tmp.alloc(&upd, 2 * K + 1));
+
+  // --- fold and w range
+  double wmin = 0.0, wmax = 0.0;
+  if (M > 0) {
+    fold_kernel<<<nblk, kPlanThreads, 0, s>>>(uvw, M, d.conj_fold ? 1 : 0, w_fold, flag, pmin,
+                                              pmax);
+    PHI_CUDA_TRY(cudaGetLastError());
+    std::vector<double> hmin(nblk), hmax(nblk);
+    PHI_CUDA_TRY(cudaMemcpyAsync(hmin.data(), pmin, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaMemcpyAsync(hmax.data(), pmax, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+    wmin = *std::min_element(hmin.begin(), hmin.end());
+    wmax = *std::max_element(hmax.begin(), hmax.end());
+  }
+
+  // --- Algorithm 1
+  std::vector<double> c(K);
+  for (int q = 0; q < K; ++q)
+    c[q] = (K == 1) ? 0.5 * (wmin + wmax) : wmin + q * (wmax - wmin) / (K - 1);
+  double eps = (wmax - wmin) / K;
+  if (!(eps > 0.0)) eps = 1.0;
+  PHI_CUDA_TRY(cudaMemcpyAsync(centres, c.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  std::vector<double> hupd(2 * K + 1);
+  p.kmeans_sweeps = 0;
+  if (M > 0) {
+    const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
+    const size_t smem = sizeof(double) * (K + 2 * (kPlanThreads / 32) * K);
+    while (p.kmeans_sweeps < d.kmeans_max_iter) {
+      ++p.kmeans_sweeps;
+      kmeans_sweep_kernel<<<nblk, kPlanThreads, smem, s>>>(w_fold, M, chunk, centres, K, stack,
+                                                           psum, pcnt);
+      PHI_CUDA_TRY(cudaGetLastError());
+      kmeans_update_kernel<<<1, 128, 0, s>>>(psum, pcnt, nblk, K, eps, centres, upd);
+      PHI_CUDA_TRY(cudaGetLastError());
+      PHI_CUDA_TRY(cudaMemcpyAsync(hupd.data(), upd, sizeof(double) * (2 * K + 1),
+                                   cudaMemcpyDeviceToHost, s));
+      PHI_CUDA_TRY(cudaStreamSynchronize(s));
+      if (hupd[2 * K] < d.kmeans_tol) break;
+    }
+    for (int q = 0; q < K; ++q) p.wbar[q] = hupd[q];
+  } else {
+    for (int q = 0; q < K; ++q) p.wbar[q] = c[q];
+  }
+
+  // --- classify: drop test, keys, per-stack max |dw| and kept counts
+  const int tile = d.tile > 0 ? d.tile : 32;
+  const int tiles_per_row = (p.npad + tile - 1) / tile;
+  if (static_cast<int64_t>(tiles_per_row) * tiles_per_row >= (1 << 24)) return PHI_ERR_ARG;
+  uint32_t *keys = nullptr, *vals = nullptr, *skeys = nullptr, *svals = nullptr;
+  unsigned long long* stat = nullptr;  // [0..K) max |dw| bits, [K..2K) kept, [2K..3K) max jw
+  PHI_CUDA_TRY(tmp.alloc(&keys, M));
+  PHI_CUDA_TRY(tmp.alloc(&vals, M));
+  PHI_CUDA_TRY(tmp.alloc(&skeys, M));
+  PHI_CUDA_TRY(tmp.alloc(&svals, M));
+  PHI_CUDA_TRY(tmp.alloc(&stat, 3 * static_cast<size_t>(K)));
+  PHI_CUDA_TRY(cudaMemsetAsync(stat, 0, sizeof(unsigned long long) * 3 * K, s));
+  std::vector<unsigned long long> hstat(3 * K, 0);
+  if (M > 0) {
+    classify_kernel<<<nblk, kPlanThreads, 0, s>>>(uvw, flag, w_fold, stack, centres, M, K, p.du,
+                                                  p.npad, tile, tiles_per_row, keys, vals, stat,
+                                                  stat + K);
+    PHI_CUDA_TRY(cudaGetLastError());
+    PHI_CUDA_TRY(cudaMemcpyAsync(hstat.data(), stat, sizeof(unsigned long long) * 2 * K,
+                                 cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  p.n_kept = 0;
+  for (int q = 0; q < K; ++q) {
+    p.stack_off[q] = p.n_kept;
+    p.n_kept += static_cast<int64_t>(hstat[K + q]);
+    double maxabs;
+    unsigned long long bits = hstat[q];
+    std::memcpy(&maxabs, &bits, sizeof(double));
+    p.stack_jw[q] = hstat[K + q] ? d.support + 2 * static_cast<int32_t>(std::ceil(maxabs * p.c_support)) : 0;
+  }
+  p.stack_off[K] = p.n_kept;
+  p.n_dropped = M - p.n_kept;
+  // The per-visibility rule never exceeds the per-stack one, so checking the
+  // per-stack value covers both.
+  p.max_jw = 0;
+  for (int q = 0; q < K; ++q) p.max_jw = std::max(p.max_jw, p.stack_jw[q]);
+  if (p.max_jw > d.max_support) return PHI_ERR_SUPPORT;
+
+  // --- sort by (stack, tile); dropped visibilities go last and are not kept
+  if (M > 0) {
+    size_t temp_bytes = 0;
+    cub::DeviceRadixSort::SortPairs(nullptr, temp_bytes, keys, skeys, vals, svals,
+                                    static_cast<int>(M), 0, 32, s);
+    void* temp = nullptr;
+    PHI_CUDA_TRY(tmp.alloc(reinterpret_cast<unsigned char**>(&temp), temp_bytes));
+    if (cub::DeviceRadixSort::SortPairs(temp, temp_bytes, keys, skeys, vals, svals,
+                                        static_cast<int>(M), 0, 32, s) != cudaSuccess)
+      return PHI_ERR_CUDA;
+  }
+
+  // --- records
+  int32_t* d_stack_jw = nullptr;
+  PHI_CUDA_TRY(tmp.alloc(&d_stack_jw, K));
+  PHI_CUDA_TRY(cudaMemcpyAsync(d_stack_jw, p.stack_jw.data(), sizeof(int32_t) * K,
+                               cudaMemcpyHostToDevice, s));
+  const bool f64 = d.precision == PHI_F64;
+  const size_t rec_bytes = f64 ? sizeof(VisRec<double>) : sizeof(VisRec<float>);
+  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.recs), rec_bytes * p.n_kept));
+  PHI_CUDA_TRY(owned_alloc(p, &p.perm, p.n_kept));
+  const int per_vis = d.support_rule == PHI_SUPPORT_VIS ? 1 : 0;
+  if (p.n_kept > 0) {
+    if (f64)
+      records_kernel<double><<<nblk, kPlanThreads, 0, s>>>(
+          uvw, flag, w_fold, stack, centres, weights, svals, p.n_kept, p.du, d.support,
+          p.c_support, per_vis, d_stack_jw, static_cast<VisRec<double>*>(p.recs), p.perm);
+    else
+      records_kernel<float><<<nblk, kPlanThreads, 0, s>>>(
+          uvw, flag, w_fold, stack, centres, weights, svals, p.n_kept, p.du, d.support,
+          p.c_support, per_vis, d_stack_jw, static_cast<VisRec<float>*>(p.recs), p.perm);
+    PHI_CUDA_TRY(cudaGetLastError());
+  }
+
+  // --- tables, grid, FFT plan
+  const size_t tsize = f64 ? sizeof(double) : sizeof(float);
+  const int64_t nodes = panel_table_offset(kNumPanelCounts);
+  PHI_CUDA_TRY(owned_alloc(p, &p.node_omn, nodes));
+  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.node_hg), tsize * nodes));
+  PHI_CUDA_TRY(owned_alloc(p, &p.omn_pix, static_cast<size_t>(p.N) * p.N));
+  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.corr_pix),
+                           tsize * p.N * static_cast<size_t>(p.N)));
+  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.grid),
+                           2 * tsize * static_cast<size_t>(p.npad) * p.npad));
+  PHI_TRY(launch_node_tables(p, s));
+  PHI_TRY(launch_pixel_tables(p, s));
+  if (cufftCreate(&p.fft) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+  p.fft_ok = true;
+  size_t work = 0;
+  if (cufftMakePlan2d(p.fft, p.npad, p.npad, f64 ? CUFFT_Z2Z : CUFFT_C2C, &work) != CUFFT_SUCCESS)
+    return PHI_ERR_OOM;
+  p.device_bytes += static_cast<int64_t>(work);
+  PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  return PHI_OK;
+}
+
+}  // namespace
+}  // namespace phi
+
+extern "C" int phi_plan_desc_default(phi_plan_desc* d) {
+  if (!d) return PHI_ERR_ARG;
+  std::memset(d, 0, sizeof(*d));
+  d->support = 4;
+  d->n_stacks = 1;
+  d->kmeans_max_iter = 100;
+  d->conj_fold = 0;
+  d->max_support = 64;
+  d->precision = PHI_F32;
+  d->support_rule = PHI_SUPPORT_STACK;
+  d->max_refine = 3;
+  d->tile = 32;
+  d->oversample = 2.0;
+  d->kmeans_tol = 1e-3;
+  d->alpha = 1.0;
+  d->quad_rel_tol = 1e-6;
+  d->quad_abs_tol = 1e-6;
+  d->kb_beta = 0.0;
+  d->cycles_per_panel = 0.0;
+  return PHI_OK;
+}
+
+extern "C" int phi_plan_create(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
+                               const double* weights_dev, int64_t n_vis, void* stream) {
+  if (!out || !desc) return PHI_ERR_ARG;
+  *out = nullptr;
+  int st = phi::validate(*desc, n_vis);
+  if (st != PHI_OK) return st;
+  if (n_vis > 0 && !uvw_dev) return PHI_ERR_ARG;
+  phi_plan* p = new (std::nothrow) phi_plan();
+  if (!p) return PHI_ERR_OOM;
+  p->d = *desc;
+  st = phi::build(*p, uvw_dev, weights_dev, n_vis, static_cast<cudaStream_t>(stream));
+  if (st != PHI_OK) {
+    cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    phi::free_plan(p);
+    delete p;
+    return st;
+  }
+  *out = p;
+  return PHI_OK;
+}
+
+extern "C" void phi_plan_destroy(phi_plan_t plan) {
+  if (!plan) return;
+  phi::free_plan(plan);
+  delete plan;
+}
+
+extern "C" int phi_plan_info(phi_plan_t plan, phi_plan_summary* info, double* wbar, int64_t* counts,
+                             int32_t* jw) {
+  if (!plan) return PHI_ERR_ARG;
+  const phi::Plan& p = *plan;
+  if (info) {
+    info->n_vis = p.M;
+    info->n_kept = p.n_kept;
+    info->n_dropped = p.n_dropped;
+    info->device_bytes = p.device_bytes;
+    info->image_n = p.N;
+    info->npad = p.npad;
+    info->n_stacks = p.K;
+    info->kmeans_sweeps = p.kmeans_sweeps;
+    info->max_jw = p.max_jw;
+    info->precision = p.d.precision;
+    info->du = p.du;
+    info->dl = p.dl;
+    info->beta = p.beta;
+    info->window_radius = p.R;
+    info->support_coeff = p.c_support;
+  }
+  for (int q = 0; q < p.K; ++q) {
+    if (wbar) wbar[q] = p.wbar[q];
+    if (counts) counts[q] = p.stack_off[q + 1] - p.stack_off[q];
+    if (jw) jw[q] = p.stack_jw[q];
+  }
+  return PHI_OK;
+}
+
+extern "C" int phi_plan_stats(phi_plan_t plan, int64_t* n_unconverged, int64_t* n_taps,
+                              int64_t* n_tap_nodes, int reset, void* stream) {
+  if (!plan) return PHI_ERR_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  unsigned long long h[4] = {0, 0, 0, 0};
+  PHI_CUDA_TRY(cudaMemcpyAsync(h, plan->counters + plan->K, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  if (n_unconverged) *n_unconverged = static_cast<int64_t>(h[0]);
+  if (n_taps) *n_taps = static_cast<int64_t>(h[1]);
+  if (n_tap_nodes) *n_tap_nodes = static_cast<int64_t>(h[3]);
+  if (reset) {
+    PHI_CUDA_TRY(cudaMemsetAsync(plan->counters + plan->K, 0, 4 * sizeof(unsigned long long), s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return PHI_OK;
+}
+
+extern "C" const char* phi_error_string(int status) {
+  switch (status) {
+    case PHI_OK: return "ok";
+    case PHI_ERR_ARG: return "invalid argument";
+    case PHI_ERR_OOM: return "device out of memory";
+    case PHI_ERR_CUDA: return "CUDA or cuFFT call failed";
+    case PHI_ERR_HORIZON: return "image or kernel window reaches the horizon";
+    case PHI_ERR_SUPPORT: return "w-projection support exceeds max_support";
+    case PHI_ERR_TIMEOUT: return "bounded wait timed out";
+    case PHI_ERR_STATE: return "call does not apply to this plan";
+    default: return "unknown status";
+  }
+}
