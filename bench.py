@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--support-rule", default="stack", choices=["stack", "vis"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--max-vis", type=int, default=0,
+                    help="use only the first N visibilities (small profiling case)")
     return ap.parse_args()
 
 
@@ -216,7 +218,7 @@ def run_reference(args, ws, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / len(per_step),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": wl.name, "image_n": wl.image_n, "n_stacks": wl.n_stacks,
+            "config": {"workload": wl.name + (f"-first{M}" if args.max_vis else ""), "image_n": wl.image_n, "n_stacks": wl.n_stacks,
                        "quad_tol": 1e-6, "sample_per_step": n_tot},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n_tot} random kept visibilities per step, degrid+grid, "
@@ -234,6 +236,8 @@ def run_ours(args, ws, rank, local):
     dev = torch.device("cuda", torch.cuda.current_device())
     wl = W.mwa_snapshot(seed=0)
     uvw_np, x_np = workload_inputs(wl)
+    if args.max_vis:
+        uvw_np = np.ascontiguousarray(uvw_np[:args.max_vis])
     M = len(uvw_np)
     desc = dict(image_n=wl.image_n, fov_rad=math.radians(wl.fov_deg), oversample=wl.oversample,
                 support=wl.support, n_stacks=wl.n_stacks, conj_fold=int(wl.conj_fold),
@@ -308,13 +312,13 @@ def run_ours(args, ws, rank, local):
     clocks = clk.summary()
 
     # end to end through the public API from pinned host buffers
-    e2e = run_e2e(phi, desc, uvw_np, x_np, args.e2e_steps, dev)
+    e2e = run_e2e(phi, desc, uvw_np, x_np, args.e2e_steps, dev) if args.e2e_steps > 0 else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": wl.name, "image_n": wl.image_n, "npad": info["npad"],
+        "config": {"workload": wl.name + (f"-first{M}" if args.max_vis else ""), "image_n": wl.image_n, "npad": info["npad"],
                    "fov_deg": wl.fov_deg, "n_vis": M, "n_kept": n_kept,
                    "n_dropped": info["n_dropped"], "n_stacks": wl.n_stacks, "conj_fold": wl.conj_fold,
                    "support": wl.support, "support_rule": args.support_rule,

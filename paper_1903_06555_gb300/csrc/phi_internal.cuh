@@ -9,7 +9,10 @@
 //   omn_pix[N*N]        1 - n(l, m) per pixel (FP64, for the chirp phase);
 //   corr_pix[N*N]       1 / (g(du |l|) n(l, m)) per pixel (precision T);
 //   node tables         per admissible panel count P: 1 - n(r_j) (FP64) and
-//                       2 pi h g(r_j) r_j (T) at the 15 P Gauss-Kronrod nodes;
+//                       w 2 pi h g(r_j) r_j (T, Kronrod and Kronrod-minus-
+//                       Gauss weights w) at the 15 P Gauss-Kronrod nodes;
+//   tap order           per even support J_w, its J_w^2 taps sorted by
+//                       distance from the box centre (uint16 a | b << 8);
 //   grid[Npad*Npad]     one padded complex grid reused by every stack;
 //   counters            work-queue heads and quadrature statistics.
 #pragma once
@@ -76,6 +79,12 @@ struct __align__(16) VisRec<double> {
   int32_t pad;
 };
 
+// Shared per-node integrand values of one visibility, with the Kronrod
+// weight (k) and the Kronrod-minus-Gauss weight (d) folded in.
+template <typename T> struct NodeVal;
+template <> struct __align__(16) NodeVal<float> { float kr, ki, dr, di; };
+template <> struct __align__(16) NodeVal<double> { double kr, ki, dr, di; };
+
 // Kernel-side constants of one plan.
 struct QuadParams {
   double R;               // window radius (r units)
@@ -86,7 +95,10 @@ struct QuadParams {
   int max_refine;         // panel-count doublings allowed
   int npad;
   const double* node_omn;  // 1 - n(r_j) per node, all panel counts
-  const void* node_hg;     // 2 pi h g(r_j) r_j per node (T)
+  const void* node_hk;     // w_K(j) 2 pi h g(r_j) r_j per node (T)
+  const void* node_hd;     // (w_K(j) - w_G(j)) 2 pi h g(r_j) r_j per node (T)
+  const uint16_t* tap_order;  // per even J_w: taps (a | b << 8) by distance from the box centre
+  const int32_t* tap_off;     // offset of the list for J_w = 2 i + 2 at index i
 };
 
 struct Plan {
@@ -106,7 +118,10 @@ struct Plan {
   double* omn_pix = nullptr;
   void* corr_pix = nullptr;
   double* node_omn = nullptr;
-  void* node_hg = nullptr;
+  void* node_hk = nullptr;
+  void* node_hd = nullptr;
+  uint16_t* tap_order = nullptr;
+  int32_t* tap_off = nullptr;
   void* grid = nullptr;
   // [0..K) work heads, [K] unconverged taps, [K+1] taps, [K+2] wkernel misses,
   // [K+3] tap-node evaluations
@@ -133,7 +148,10 @@ struct Plan {
     q.max_refine = d.max_refine;
     q.npad = npad;
     q.node_omn = node_omn;
-    q.node_hg = node_hg;
+    q.node_hk = node_hk;
+    q.node_hd = node_hd;
+    q.tap_order = tap_order;
+    q.tap_off = tap_off;
     return q;
   }
 };

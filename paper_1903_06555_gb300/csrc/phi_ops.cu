@@ -20,6 +20,7 @@
 // transpose pair exactly.
 #include <cuda_runtime.h>
 
+#include "bessel_j0.cuh"
 #include "phi_internal.cuh"
 
 namespace phi {
@@ -64,11 +65,31 @@ __host__ __device__ constexpr double gk_wd(int j) {  // Kronrod minus Gauss weig
   return gk_kronrod_weight(gk_fold(j)) - gk_gauss_weight(gk_fold(j));
 }
 
+// Nodes in the precision of the integrand, read uniformly by the whole warp.
+__constant__ float c_gk_node_f[15] = {
+    -0.991455371120812639f, -0.949107912342758525f, -0.864864423359769073f,
+    -0.741531185599394440f, -0.586087235467691130f, -0.405845151377397167f,
+    -0.207784955007898468f, 0.0f, 0.207784955007898468f, 0.405845151377397167f,
+    0.586087235467691130f, 0.741531185599394440f, 0.864864423359769073f,
+    0.949107912342758525f, 0.991455371120812639f};
+__constant__ double c_gk_node_d[15] = {
+    -0.991455371120812639206854697526329, -0.949107912342758524526189684047851,
+    -0.864864423359769072789712788640926, -0.741531185599394439863864773280788,
+    -0.586087235467691130294144845693013, -0.405845151377397166906606412076961,
+    -0.207784955007898467600689403773245, 0.0, 0.207784955007898467600689403773245,
+    0.405845151377397166906606412076961, 0.586087235467691130294144845693013,
+    0.741531185599394439863864773280788, 0.864864423359769072789712788640926,
+    0.949107912342758524526189684047851, 0.991455371120812639206854697526329};
+
 // ---------------------------------------------------------------------------
 // Small helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float bessel_j0(float x) { return j0f(x); }
-__device__ __forceinline__ double bessel_j0(double x) { return j0(x); }
+// J0(pi u): the FP32 path uses the compact approximation of bessel_j0.cuh,
+// the FP64 path CUDA's j0.
+__device__ __forceinline__ float j0_hc(float u) { return j0_halfcycles(u); }
+__device__ __forceinline__ double j0_hc(double u) { return j0(kPi * u); }
+__device__ __forceinline__ float gk_node_c(float, int j) { return c_gk_node_f[j]; }
+__device__ __forceinline__ double gk_node_c(double, int j) { return c_gk_node_d[j]; }
 __device__ __forceinline__ void sincos_pi(float a, float* s, float* c) { sincospif(a, s, c); }
 __device__ __forceinline__ void sincos_pi(double a, double* s, double* c) { sincospi(a, s, c); }
 
@@ -115,7 +136,7 @@ __device__ double taper_g(double r, double a, double beta, double i0beta) {
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void node_table_kernel(double R, double du, double a, double beta, double* omn,
-                                  T* hg, int64_t total) {
+                                  T* hk, T* hd, int64_t total) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= total) return;
   int i = 0;
@@ -129,12 +150,13 @@ __global__ void node_table_kernel(double R, double du, double a, double beta, do
   int p = static_cast<int>(local / 15);
   int k = static_cast<int>(local % 15);
   double hw = R / (2.0 * npan);
-  double xk = k < 7 ? -gk_abs_node(k) : gk_abs_node(14 - k);
-  double r = hw * (2.0 * p + 1.0 + xk);
+  double r = hw * (2.0 * p + 1.0 + gk_node(k));
   double l = r / du;
   double s = l * l;
   omn[j] = s / (1.0 + sqrt(1.0 - s));
-  hg[j] = static_cast<T>(2.0 * kPi * hw * taper_g(r, a, beta, cyl_bessel_i0(beta)) * r);
+  double h = 2.0 * kPi * hw * taper_g(r, a, beta, cyl_bessel_i0(beta)) * r;
+  hk[j] = static_cast<T>(gk_wk(k) * h);
+  hd[j] = static_cast<T>(gk_wd(k) * h);
 }
 
 template <typename T>
@@ -157,10 +179,12 @@ int launch_node_tables(Plan& p, cudaStream_t s) {
   double a = 0.5 * p.d.support;
   if (p.d.precision == PHI_F64)
     node_table_kernel<double><<<blocks, 256, 0, s>>>(p.R, p.du, a, p.beta, p.node_omn,
-                                                    static_cast<double*>(p.node_hg), total);
+                                                    static_cast<double*>(p.node_hk),
+                                                    static_cast<double*>(p.node_hd), total);
   else
     node_table_kernel<float><<<blocks, 256, 0, s>>>(p.R, p.du, a, p.beta, p.node_omn,
-                                                   static_cast<float*>(p.node_hg), total);
+                                                   static_cast<float*>(p.node_hk),
+                                                   static_cast<float*>(p.node_hd), total);
   PHI_CUDA_TRY(cudaGetLastError());
   return PHI_OK;
 }
@@ -244,89 +268,91 @@ __global__ void finish_kernel(const C* __restrict__ grid, const double* __restri
 // Fused kernel quadrature
 // ---------------------------------------------------------------------------
 
-// Build h(r_j) for panels [p0, p0 + np) of the npan-panel partition.
-template <typename T, typename C>
-__device__ __forceinline__ void build_nodes(C* sh, const QuadParams& q, int pidx, int p0, int np,
-                                            double dw, int lane) {
+// Build the weighted integrand values for panels [p0, p0 + np) of the
+// npan-panel partition: h(r_j) e^{2 pi i dw (1 - n(r_j))}, phase argument in FP64.
+template <typename T>
+__device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q, int pidx, int p0,
+                                            int np, double dw, int lane) {
   const int64_t off = panel_table_offset(pidx) + 15 * (int64_t)p0;
   const double* omn = q.node_omn + off;
-  const T* hg = static_cast<const T*>(q.node_hg) + off;
+  const T* hk = static_cast<const T*>(q.node_hk) + off;
+  const T* hd = static_cast<const T*>(q.node_hd) + off;
   for (int j = lane; j < 15 * np; j += 32) {
     double t = dw * omn[j];
     t -= rint(t);
     T sn, cs;
     sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
-    T h = hg[j];
-    C v;
-    v.x = h * cs;
-    v.y = h * sn;
+    const T k = hk[j], d = hd[j];
+    NodeVal<T> v;
+    v.kr = k * cs;
+    v.ki = k * sn;
+    v.dr = d * cs;
+    v.di = d * sn;
     sh[j] = v;
   }
 }
 
-// Sum panels [0, np) held in sh (global panel index p0 + p) for one tap.
-template <typename T, typename C>
-__device__ __forceinline__ void eval_panels(const C* sh, int p0, int np, T B, C& acc,
-                                            double& err) {
+// Accumulate panels [0, np) held in sh (global panel index p0 + p) for one
+// tap: Bh = 2 rho h (half-cycles of J0 per unit of the node coordinate).
+template <typename T>
+__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np, T Bh, T& kr,
+                                            T& ki, T& err) {
   for (int p = 0; p < np; ++p) {
-    const T a = B * static_cast<T>(2 * (p0 + p) + 1);
-    T kr = 0, ki = 0, dr = 0, di = 0;
-    const C* hp = sh + 15 * p;
-#pragma unroll
+    const T a = Bh * static_cast<T>(2 * (p0 + p) + 1);
+    const NodeVal<T>* hp = sh + 15 * p;
+    T dr = 0, di = 0;
+#pragma unroll 5
     for (int j = 0; j < 15; ++j) {
-      const T x = fma(B, static_cast<T>(gk_node(j)), a);
-      const T J = bessel_j0(x);
-      const C h = hp[j];
-      const T tr = J * h.x, ti = J * h.y;
-      kr = fma(static_cast<T>(gk_wk(j)), tr, kr);
-      ki = fma(static_cast<T>(gk_wk(j)), ti, ki);
-      dr = fma(static_cast<T>(gk_wd(j)), tr, dr);
-      di = fma(static_cast<T>(gk_wd(j)), ti, di);
+      const T u = fma(Bh, gk_node_c(T(0), j), a);
+      const T J = j0_hc(u);
+      const NodeVal<T> v = hp[j];
+      kr = fma(J, v.kr, kr);
+      ki = fma(J, v.ki, ki);
+      dr = fma(J, v.dr, dr);
+      di = fma(J, v.di, di);
     }
-    acc.x += kr;
-    acc.y += ki;
-    err += static_cast<double>(sqrt(dr * dr + di * di));
+    err += sqrt(dr * dr + di * di);
   }
 }
 
 __device__ __forceinline__ int next_panel_index(int pidx) { return pidx == 0 ? 1 : pidx + 2; }
 
 // Evaluate [GC](rho, dw) for one tap per lane (inactive lanes compute a
-// harmless dummy).  pidx and built (the panel-count index whose nodes are
-// resident in sh, or -1) are warp-uniform and updated in place.
+// harmless dummy) with the panel-count index pidx, refining the whole chunk
+// while any active tap misses the tolerance.  `built` (the panel-count index
+// whose nodes are resident in sh, or -1) is warp-uniform and updated.
 template <typename T, typename C>
-__device__ C eval_chunk(C* sh, const QuadParams& q, T rho, bool active, double dw, int& pidx,
-                        int& built, bool& ok, int lane, unsigned long long& nodes) {
+__device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active, double dw,
+                        int pidx, int& built, bool& ok, int lane, unsigned long long& nodes) {
   int refine = 0;
   while (true) {
     const int npan = panel_count_at(pidx);
     nodes += active ? 15ull * npan : 0ull;
-    const T B = static_cast<T>(2.0 * kPi * (q.R / (2.0 * npan))) * rho;
-    C acc = cmake<C>(0.0, 0.0);
-    double err = 0.0;
+    const T Bh = static_cast<T>(q.R / npan) * rho;   // 2 rho (R / (2 npan))
+    T kr = 0, ki = 0, err = 0;
     if (npan <= kPanelBatch) {
       if (built != pidx) {
         __syncwarp();
-        build_nodes<T, C>(sh, q, pidx, 0, npan, dw, lane);
+        build_nodes<T>(sh, q, pidx, 0, npan, dw, lane);
         __syncwarp();
         built = pidx;
       }
-      eval_panels<T, C>(sh, 0, npan, B, acc, err);
+      eval_panels<T>(sh, 0, npan, Bh, kr, ki, err);
     } else {
       for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
         const int nb = min(kPanelBatch, npan - p0);
         __syncwarp();
-        build_nodes<T, C>(sh, q, pidx, p0, nb, dw, lane);
+        build_nodes<T>(sh, q, pidx, p0, nb, dw, lane);
         __syncwarp();
-        eval_panels<T, C>(sh, p0, nb, B, acc, err);
+        eval_panels<T>(sh, p0, nb, Bh, kr, ki, err);
       }
       built = -1;
     }
-    const double mag = sqrt(static_cast<double>(acc.x) * acc.x + static_cast<double>(acc.y) * acc.y);
-    ok = (!active) || err <= fmax(q.tol_abs, q.tol_rel * mag);
+    const double mag = sqrt(static_cast<double>(kr) * kr + static_cast<double>(ki) * ki);
+    ok = (!active) || static_cast<double>(err) <= fmax(q.tol_abs, q.tol_rel * mag);
     const bool any_bad = __any_sync(0xffffffffu, !ok);
     const int nxt = next_panel_index(pidx);
-    if (!any_bad || refine >= q.max_refine || nxt >= kNumPanelCounts) return acc;
+    if (!any_bad || refine >= q.max_refine || nxt >= kNumPanelCounts) return cmake<C>(kr, ki);
     ++refine;
     pidx = nxt;
   }
@@ -338,19 +364,21 @@ __device__ __forceinline__ int initial_panel_index(const QuadParams& q, T rho_ma
   return panel_count_index_for(cyc / q.cycles_per_panel);
 }
 
-// One warp per visibility, visibilities taken from a work queue.
+// One warp per visibility, visibilities taken from a work queue.  Taps are
+// visited in order of distance from the box centre, 32 at a time; each
+// chunk takes the panel count its farthest tap needs.
 template <typename T, typename C, bool kGrid>
-__global__ void __launch_bounds__(256) vis_kernel(const VisRec<T>* __restrict__ recs,
-                                                  const uint32_t* __restrict__ perm, int64_t n,
-                                                  const C* __restrict__ grid_in, C* grid_out,
-                                                  const C* __restrict__ vis_in,
-                                                  C* __restrict__ vis_out, QuadParams q,
-                                                  unsigned long long* head,
-                                                  unsigned long long* stats) {
+__global__ void __launch_bounds__(256, 2) vis_kernel(const VisRec<T>* __restrict__ recs,
+                                                     const uint32_t* __restrict__ perm, int64_t n,
+                                                     const C* __restrict__ grid_in, C* grid_out,
+                                                     const C* __restrict__ vis_in,
+                                                     C* __restrict__ vis_out, QuadParams q,
+                                                     unsigned long long* head,
+                                                     unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  C* sh = reinterpret_cast<C*>(smem_raw) + warp * kNodeBatch;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int64_t npad = q.npad;
   while (true) {
@@ -362,9 +390,7 @@ __global__ void __launch_bounds__(256) vis_kernel(const VisRec<T>* __restrict__ 
     const int Jw = r.jw;
     const int half = Jw / 2;
     const T fu = r.fu, fv = r.fv;
-    const T mu = fmax(fu + static_cast<T>(half - 1), static_cast<T>(half) - fu);
-    const T mv = fmax(fv + static_cast<T>(half - 1), static_cast<T>(half) - fv);
-    int pidx = initial_panel_index<T>(q, sqrt(mu * mu + mv * mv), r.dw);
+    const uint16_t* order = q.tap_order + q.tap_off[half - 1];
     int built = -1;
     const uint32_t pm = perm[i];
     C yv = cmake<C>(0.0, 0.0);
@@ -379,11 +405,15 @@ __global__ void __launch_bounds__(256) vis_kernel(const VisRec<T>* __restrict__ 
     for (int t0 = 0; t0 < ntap; t0 += 32) {
       const int t = t0 + lane;
       const bool active = t < ntap;
-      const int a = active ? t % Jw : 0;
-      const int b = active ? t / Jw : 0;
-      const int ou = a - half + 1, ov = b - half + 1;
+      const uint32_t code = order[active ? t : 0];
+      const int ou = static_cast<int>(code & 0xffu) - half + 1;
+      const int ov = static_cast<int>(code >> 8) - half + 1;
       const T du_ = fu - static_cast<T>(ou), dv_ = fv - static_cast<T>(ov);
       const T rho = sqrt(du_ * du_ + dv_ * dv_);
+      T rmax = active ? rho : T(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      const int pidx = initial_panel_index<T>(q, rmax, r.dw);
       bool ok = true;
       const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, pidx, built, ok, lane, my_nodes);
       if (active) {
@@ -439,16 +469,16 @@ __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
-  C* sh = reinterpret_cast<C*>(smem_raw) + warp * kNodeBatch;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   const int64_t wpb = blockDim.x >> 5;
   for (int64_t i = blockIdx.x * wpb + warp; i < n; i += (int64_t)gridDim.x * wpb) {
     const T rho = static_cast<T>(rho_in[i]);
     const double dw = dw_in[i];
-    int pidx = initial_panel_index<T>(q, rho, dw);
     int built = -1;
     bool ok = true;
     unsigned long long nodes = 0;
-    const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw, pidx, built, ok, lane, nodes);
+    const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw, initial_panel_index<T>(q, rho, dw),
+                                 built, ok, lane, nodes);
     if (lane == 0) {
       out[i] = K;
       if (!ok) atomicAdd(bad, 1ULL);
@@ -475,7 +505,7 @@ int blocks_for_vis(const Plan& p, size_t smem) {
 
 template <typename T, typename C>
 int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
-  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(C);
+  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
   long ev = timer_begin(p, s);
   PHI_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(C) * (size_t)p.M, s));
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
@@ -515,7 +545,7 @@ int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
 
 template <typename T, typename C>
 int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
-  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(C);
+  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
   const int vis_blocks = blocks_for_vis<T, C>(p, smem);
   const int img_blocks = p.num_sms * 8;
@@ -563,7 +593,7 @@ int run_wkernel(Plan& p, const double* rho, const double* dw, int64_t n, C* out,
   unsigned long long* bad = p.counters + p.K + 2;
   PHI_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
   if (n > 0) {
-    const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(C);
+    const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
     int64_t want = (n + 7) / 8;
     int blocks = static_cast<int>(want < 65535 ? want : 65535);
     wkernel_kernel<T, C><<<blocks, kVisThreads, smem, s>>>(rho, dw, n, out, p.quad(), bad);
@@ -599,8 +629,8 @@ void timer_end(Plan& p, long idx, int stage, cudaStream_t s) {
 }
 
 int set_kernel_smem_limits() {
-  const size_t f32 = (kVisThreads / 32) * kNodeBatch * sizeof(float2);
-  const size_t f64 = (kVisThreads / 32) * kNodeBatch * sizeof(double2);
+  const size_t f32 = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<float>);
+  const size_t f64 = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<double>);
   PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<float, float2, false>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32));
   PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<float, float2, true>,

@@ -246,7 +246,10 @@ void free_plan(Plan* p) {
   cudaFree(p->omn_pix);
   cudaFree(p->corr_pix);
   cudaFree(p->node_omn);
-  cudaFree(p->node_hg);
+  cudaFree(p->node_hk);
+  cudaFree(p->node_hd);
+  cudaFree(p->tap_order);
+  cudaFree(p->tap_off);
   cudaFree(p->grid);
   cudaFree(p->counters);
 }
@@ -287,6 +290,37 @@ int validate(const phi_plan_desc& d, int64_t M) {
   if (d.max_refine < 0 || d.max_refine > 8) return PHI_ERR_ARG;
   if (d.tile < 0 || d.tile > 4096) return PHI_ERR_ARG;
   if (d.kb_beta < 0.0 || d.cycles_per_panel < 0.0) return PHI_ERR_ARG;
+  return PHI_OK;
+}
+
+// Taps of every even support J <= jmax, each list sorted by distance of the
+// tap (a, b) from the box centre (J/2 - 1/2, J/2 - 1/2), ties in raster order.
+// A pure index permutation: it changes the order taps are visited in, never
+// which taps are used.
+int build_tap_order(Plan& p, int jmax, cudaStream_t s) {
+  std::vector<int32_t> off;
+  std::vector<uint16_t> codes;
+  for (int J = 2; J <= jmax; J += 2) {
+    off.push_back(static_cast<int32_t>(codes.size()));
+    std::vector<std::pair<int, int>> taps;
+    for (int b = 0; b < J; ++b)
+      for (int a = 0; a < J; ++a) {
+        const int da = 2 * a - (J - 1), db = 2 * b - (J - 1);
+        taps.emplace_back(da * da + db * db, a | (b << 8));
+      }
+    std::stable_sort(taps.begin(), taps.end(),
+                     [](const std::pair<int, int>& x, const std::pair<int, int>& y) {
+                       return x.first < y.first;
+                     });
+    for (const auto& t : taps) codes.push_back(static_cast<uint16_t>(t.second));
+  }
+  PHI_CUDA_TRY(owned_alloc(p, &p.tap_order, codes.size()));
+  PHI_CUDA_TRY(owned_alloc(p, &p.tap_off, off.size()));
+  PHI_CUDA_TRY(cudaMemcpyAsync(p.tap_order, codes.data(), codes.size() * sizeof(uint16_t),
+                               cudaMemcpyHostToDevice, s));
+  PHI_CUDA_TRY(cudaMemcpyAsync(p.tap_off, off.data(), off.size() * sizeof(int32_t),
+                               cudaMemcpyHostToDevice, s));
+  PHI_CUDA_TRY(cudaStreamSynchronize(s));
   return PHI_OK;
 }
 
@@ -468,7 +502,9 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   const size_t tsize = f64 ? sizeof(double) : sizeof(float);
   const int64_t nodes = panel_table_offset(kNumPanelCounts);
   PHI_CUDA_TRY(owned_alloc(p, &p.node_omn, nodes));
-  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.node_hg), tsize * nodes));
+  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.node_hk), tsize * nodes));
+  PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.node_hd), tsize * nodes));
+  PHI_TRY(build_tap_order(p, std::max(p.max_jw, 2), s));
   PHI_CUDA_TRY(owned_alloc(p, &p.omn_pix, static_cast<size_t>(p.N) * p.N));
   PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.corr_pix),
                            tsize * p.N * static_cast<size_t>(p.N)));
