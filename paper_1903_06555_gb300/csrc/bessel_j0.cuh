@@ -16,6 +16,10 @@
 #define PHI_HD __host__ __device__
 #endif
 
+#if !defined(__CUDA_ARCH__)
+#include <cstring>
+#endif
+
 namespace phi {
 
 PHI_HD inline float j0_fma(float a, float b, float c) {
@@ -34,12 +38,30 @@ PHI_HD inline float j0_rsqrt(float x) {
 #endif
 }
 
+PHI_HD inline int j0_float_bits(float x) {
+#if defined(__CUDA_ARCH__)
+  return __float_as_int(x);
+#else
+  int b;
+  memcpy(&b, &x, sizeof(b));
+  return b;
+#endif
+}
+
+PHI_HD inline float j0_bits_float(int b) {
+#if defined(__CUDA_ARCH__)
+  return __int_as_float(b);
+#else
+  float x;
+  memcpy(&x, &b, sizeof(x));
+  return x;
+#endif
+}
+
 PHI_HD inline float j0_halfcycles(float u) {
-  const float kPiF32 = 3.14159265358979f;
-  const float x = kPiF32 * u;
-  if (x <= 3.0f) {
-    // 9.4.1 in z = (x/3)^2
-    const float z = x * x * (1.0f / 9.0f);
+  if (u <= 0.954929658551372f) {  // x = pi u <= 3
+    // 9.4.1 in z = (x/3)^2 = u^2 pi^2 / 9
+    const float z = (u * u) * 1.096622711232151f;
     float p = 0.0002100f;
     p = j0_fma(p, z, -0.0039444f);
     p = j0_fma(p, z, 0.0444479f);
@@ -48,27 +70,35 @@ PHI_HD inline float j0_halfcycles(float u) {
     p = j0_fma(p, z, -2.2499997f);
     return j0_fma(p, z, 1.0f);
   }
-  // 9.4.3 with t = 3/x = 3 s, s = 1/x
-  const float r = j0_rsqrt(x);
+  // 9.4.3 with t = 3/x, x = pi u.  With r = u^{-1/2} and s = r^2 = 1/u:
+  // x^{-1/2} = r / sqrt(pi), t^k = (3/pi)^k s^k; both factors are folded
+  // into the coefficients below.
+  const float r = j0_rsqrt(u);
   const float s = r * r;
-  // f0 = sum a_k t^k  ->  sum (a_k 3^k) s^k
-  float f0 = 0.00014476f * 729.0f;
-  f0 = j0_fma(f0, s, -0.00072805f * 243.0f);
-  f0 = j0_fma(f0, s, 0.00137237f * 81.0f);
-  f0 = j0_fma(f0, s, -0.00009512f * 27.0f);
-  f0 = j0_fma(f0, s, -0.00552740f * 9.0f);
-  f0 = j0_fma(f0, s, -0.00000077f * 3.0f);
-  f0 = j0_fma(f0, s, 0.79788456f);
-  // (theta0 - x + pi/4) / pi = sum b_k t^k / pi, k >= 1
+  const float c1 = 0.954929658551372f;  // 3 / pi
+  const float c2 = c1 * c1, c3 = c2 * c1, c4 = c3 * c1, c5 = c4 * c1, c6 = c5 * c1;
+  const float isp = 0.564189583547756f;  // 1 / sqrt(pi)
+  float f0 = 0.00014476f * c6 * isp;
+  f0 = j0_fma(f0, s, -0.00072805f * c5 * isp);
+  f0 = j0_fma(f0, s, 0.00137237f * c4 * isp);
+  f0 = j0_fma(f0, s, -0.00009512f * c3 * isp);
+  f0 = j0_fma(f0, s, -0.00552740f * c2 * isp);
+  f0 = j0_fma(f0, s, -0.00000077f * c1 * isp);
+  f0 = j0_fma(f0, s, 0.79788456f * isp);
+  // (theta0 - x + pi/4) / pi = sum_k b_k t^k / pi, k >= 1
   const float ip = 0.318309886183791f;
-  float d = 0.00013558f * 729.0f * ip;
-  d = j0_fma(d, s, -0.00029333f * 243.0f * ip);
-  d = j0_fma(d, s, -0.00054125f * 81.0f * ip);
-  d = j0_fma(d, s, 0.00262573f * 27.0f * ip);
-  d = j0_fma(d, s, -0.00003954f * 9.0f * ip);
-  d = j0_fma(d, s, -0.04166397f * 3.0f * ip);
-  const float phi = (u - 0.25f) + d * s;
-  const float n = rintf(phi);
+  float d = 0.00013558f * c6 * ip;
+  d = j0_fma(d, s, -0.00029333f * c5 * ip);
+  d = j0_fma(d, s, -0.00054125f * c4 * ip);
+  d = j0_fma(d, s, 0.00262573f * c3 * ip);
+  d = j0_fma(d, s, -0.00003954f * c2 * ip);
+  d = j0_fma(d, s, -0.04166397f * c1 * ip);
+  const float phi = j0_fma(d, s, u - 0.25f);
+  // Round to the nearest integer n with the 1.5 * 2^23 shift (exact for
+  // |phi| < 2^22); the low mantissa bit of the shifted value is n's parity.
+  const float big = 12582912.0f;
+  const float shifted = phi + big;
+  const float n = shifted - big;
   const float f = phi - n;
   const float f2 = f * f;
   // cos(pi f), |f| <= 1/2: Taylor coefficients (-1)^k pi^{2k} / (2k)!
@@ -79,9 +109,9 @@ PHI_HD inline float j0_halfcycles(float u) {
   c = j0_fma(c, f2, 4.058712126416768f);
   c = j0_fma(c, f2, -4.934802200544679f);
   c = j0_fma(c, f2, 1.0f);
-  // cos(pi phi) = (-1)^n cos(pi f)
-  const float sgn = (static_cast<int>(n) & 1) ? -1.0f : 1.0f;
-  return (r * f0) * (c * sgn);
+  // cos(pi phi) = (-1)^n cos(pi f): flip the sign bit when n is odd
+  const float v = (r * f0) * c;
+  return j0_bits_float(j0_float_bits(v) ^ (j0_float_bits(shifted) << 31));
 }
 
 }  // namespace phi

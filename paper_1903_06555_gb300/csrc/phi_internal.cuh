@@ -38,7 +38,7 @@ __host__ __device__ inline int panel_count_at(int i) {
   int e = (i - 1) / 2;
   return ((i - 1) % 2 == 0 ? 2 : 3) << e;
 }
-__host__ __device__ inline int panel_count_index_for(double want) {
+__host__ __device__ inline int panel_count_index_for(float want) {
   int i = 0;
   while (i < kNumPanelCounts - 1 && panel_count_at(i) < want) ++i;
   return i;
@@ -50,7 +50,7 @@ __host__ __device__ inline int64_t panel_table_offset(int i) {
 }
 
 // Panels evaluated per batch out of the per-warp shared node buffer.
-constexpr int kPanelBatch = 32;
+constexpr int kPanelBatch = 16;
 constexpr int kNodeBatch = 15 * kPanelBatch;
 
 template <typename T> struct Cplx;
@@ -88,10 +88,10 @@ template <> struct __align__(16) NodeVal<double> { double kr, ki, dr, di; };
 // Kernel-side constants of one plan.
 struct QuadParams {
   double R;               // window radius (r units)
-  double du;              // grid spacing (wavelengths)
-  double chirp_coeff;     // local chirp frequency at r = R per unit |dw|
-  double cycles_per_panel;
-  double tol_rel, tol_abs;
+  float Rf;               // the same, for the panel-count estimate
+  float chirp_coeff;      // local chirp frequency at r = R per unit |dw|
+  float inv_cycles;       // 1 / (integrand cycles per panel)
+  float tol_rel, tol_abs;
   int max_refine;         // panel-count doublings allowed
   int npad;
   const double* node_omn;  // 1 - n(r_j) per node, all panel counts
@@ -140,9 +140,9 @@ struct Plan {
   QuadParams quad() const {
     QuadParams q;
     q.R = R;
-    q.du = du;
-    q.chirp_coeff = c_support;
-    q.cycles_per_panel = cycles_per_panel;
+    q.Rf = static_cast<float>(R);
+    q.chirp_coeff = static_cast<float>(c_support);
+    q.inv_cycles = static_cast<float>(1.0 / cycles_per_panel);
     q.tol_rel = d.quad_rel_tol;
     q.tol_abs = d.quad_abs_tol;
     q.max_refine = d.max_refine;

@@ -328,7 +328,7 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
   while (true) {
     const int npan = panel_count_at(pidx);
     nodes += active ? 15ull * npan : 0ull;
-    const T Bh = static_cast<T>(q.R / npan) * rho;   // 2 rho (R / (2 npan))
+    const T Bh = static_cast<T>(q.R / npan) * rho;   // 2 rho (R / (2 npan)), R/npan in FP64
     T kr = 0, ki = 0, err = 0;
     if (npan <= kPanelBatch) {
       if (built != pidx) {
@@ -348,8 +348,10 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
       }
       built = -1;
     }
-    const double mag = sqrt(static_cast<double>(kr) * kr + static_cast<double>(ki) * ki);
-    ok = (!active) || static_cast<double>(err) <= fmax(q.tol_abs, q.tol_rel * mag);
+    // err and |K| are both formed without cancellation (err from the
+    // Kronrod-minus-Gauss weights), so the test runs in T.
+    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * sqrt(kr * kr + ki * ki));
+    ok = (!active) || err <= lim;
     const bool any_bad = __any_sync(0xffffffffu, !ok);
     const int nxt = next_panel_index(pidx);
     if (!any_bad || refine >= q.max_refine || nxt >= kNumPanelCounts) return cmake<C>(kr, ki);
@@ -358,17 +360,17 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
   }
 }
 
-template <typename T>
-__device__ __forceinline__ int initial_panel_index(const QuadParams& q, T rho_max, double dw) {
-  double cyc = q.R * (static_cast<double>(rho_max) + fabs(dw) * q.chirp_coeff);
-  return panel_count_index_for(cyc / q.cycles_per_panel);
+// Panels for the chunk: integrand cycles over [0, R] bounded by
+// R (rho_max + |dw| chirp_coeff), at inv_cycles panels per cycle.
+__device__ __forceinline__ int initial_panel_index(const QuadParams& q, float rho_max, float adw) {
+  return panel_count_index_for(q.Rf * fmaf(adw, q.chirp_coeff, rho_max) * q.inv_cycles);
 }
 
 // One warp per visibility, visibilities taken from a work queue.  Taps are
 // visited in order of distance from the box centre, 32 at a time; each
 // chunk takes the panel count its farthest tap needs.
 template <typename T, typename C, bool kGrid>
-__global__ void __launch_bounds__(256, 2) vis_kernel(const VisRec<T>* __restrict__ recs,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const VisRec<T>* __restrict__ recs,
                                                      const uint32_t* __restrict__ perm, int64_t n,
                                                      const C* __restrict__ grid_in, C* grid_out,
                                                      const C* __restrict__ vis_in,
@@ -391,6 +393,7 @@ __global__ void __launch_bounds__(256, 2) vis_kernel(const VisRec<T>* __restrict
     const int half = Jw / 2;
     const T fu = r.fu, fv = r.fv;
     const uint16_t* order = q.tap_order + q.tap_off[half - 1];
+    const float adw = static_cast<float>(fabs(r.dw));
     int built = -1;
     const uint32_t pm = perm[i];
     C yv = cmake<C>(0.0, 0.0);
@@ -413,7 +416,7 @@ __global__ void __launch_bounds__(256, 2) vis_kernel(const VisRec<T>* __restrict
       T rmax = active ? rho : T(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-      const int pidx = initial_panel_index<T>(q, rmax, r.dw);
+      const int pidx = initial_panel_index(q, static_cast<float>(rmax), adw);
       bool ok = true;
       const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, pidx, built, ok, lane, my_nodes);
       if (active) {
@@ -477,7 +480,9 @@ __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__
     int built = -1;
     bool ok = true;
     unsigned long long nodes = 0;
-    const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw, initial_panel_index<T>(q, rho, dw),
+    const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw,
+                                 initial_panel_index(q, static_cast<float>(rho),
+                                                     static_cast<float>(fabs(dw))),
                                  built, ok, lane, nodes);
     if (lane == 0) {
       out[i] = K;
