@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--support-rule", default="stack", choices=["stack", "vis"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cycles-per-panel", type=float, default=0.0,
+                    help="a-priori quadrature panel width in integrand cycles (0: library default)")
     ap.add_argument("--max-vis", type=int, default=0,
                     help="use only the first N visibilities (small profiling case)")
     return ap.parse_args()
@@ -241,7 +243,8 @@ def run_ours(args, ws, rank, local):
     M = len(uvw_np)
     desc = dict(image_n=wl.image_n, fov_rad=math.radians(wl.fov_deg), oversample=wl.oversample,
                 support=wl.support, n_stacks=wl.n_stacks, conj_fold=int(wl.conj_fold),
-                precision="f32", support_rule=args.support_rule)
+                precision="f32", support_rule=args.support_rule,
+                cycles_per_panel=args.cycles_per_panel)
     stream = torch.cuda.current_stream()
     uvw = torch.from_numpy(uvw_np).to(dev)
     torch.cuda.synchronize()

@@ -4,12 +4,12 @@
 // Method: Abramowitz & Stegun (1964), 9.4.1 for pi u <= 3 (polynomial in
 // (x/3)^2, |error| < 5e-8) and 9.4.3 for pi u >= 3 (J0 = x^{-1/2} f0 cos theta0
 // with f0 and theta0 polynomials in 3/x, |error| < 1.6e-8 and 7e-8 rad).
-// The cosine is taken in half-cycles, cos(theta0) = cos(pi phi) with
-// phi = u - 1/4 + (theta0 - x + pi/4)/pi, reduced exactly to f = phi - n,
-// |f| <= 1/2, and evaluated with the Taylor series of cos(pi f) to degree 12
-// (truncation < 1e-8), so the whole evaluation costs one reciprocal square
-// root and ~25 FMA-pipe operations; the argument never needs a large-argument
-// trigonometric reduction.  Polynomials in s = 1/x absorb the factors 3^k.
+// The phase is carried in half-cycles, phi' = theta0/pi + 1/4 = u +
+// (theta0 - x + pi/4)/pi, reduced exactly by its nearest integer n, so the
+// cosine only ever sees an argument in [-3pi/4, pi/4]:
+// cos(theta0) = (-1)^n cos(pi (phi' - n) - pi/4).  The whole evaluation costs
+// a reciprocal square root, a short-range cosine and ~20 FMA-pipe operations.
+// Polynomials in s = 1/u absorb the factors (3/pi)^k, 1/pi and 1/sqrt(pi).
 #pragma once
 
 #ifndef PHI_HD
@@ -35,6 +35,16 @@ PHI_HD inline float j0_rsqrt(float x) {
   return rsqrtf(x);
 #else
   return 1.0f / sqrtf(x);
+#endif
+}
+
+// cos on |a| <= pi: the hardware approximation on the device (absolute
+// error ~5e-7 on this range), the libm cosine on the host.
+PHI_HD inline float j0_cos(float a) {
+#if defined(__CUDA_ARCH__)
+  return __cosf(a);
+#else
+  return cosf(a);
 #endif
 }
 
@@ -93,24 +103,16 @@ PHI_HD inline float j0_halfcycles(float u) {
   d = j0_fma(d, s, 0.00262573f * c3 * ip);
   d = j0_fma(d, s, -0.00003954f * c2 * ip);
   d = j0_fma(d, s, -0.04166397f * c1 * ip);
-  const float phi = j0_fma(d, s, u - 0.25f);
-  // Round to the nearest integer n with the 1.5 * 2^23 shift (exact for
-  // |phi| < 2^22); the low mantissa bit of the shifted value is n's parity.
+  // phi' = theta0/pi + 1/4 = u + sum_k b_k t^k / pi
+  const float phi = j0_fma(d, s, u);
+  // Round phi' to the nearest integer n with the 1.5 * 2^23 shift (exact for
+  // |phi'| < 2^22); the low mantissa bit of the shifted value is n's parity.
   const float big = 12582912.0f;
   const float shifted = phi + big;
   const float n = shifted - big;
-  const float f = phi - n;
-  const float f2 = f * f;
-  // cos(pi f), |f| <= 1/2: Taylor coefficients (-1)^k pi^{2k} / (2k)!
-  float c = 0.001929574309403923f;
-  c = j0_fma(c, f2, -0.02580689139001406f);
-  c = j0_fma(c, f2, 0.2353306303588932f);
-  c = j0_fma(c, f2, -1.335262768854589f);
-  c = j0_fma(c, f2, 4.058712126416768f);
-  c = j0_fma(c, f2, -4.934802200544679f);
-  c = j0_fma(c, f2, 1.0f);
-  // cos(pi phi) = (-1)^n cos(pi f): flip the sign bit when n is odd
-  const float v = (r * f0) * c;
+  // cos(theta0) = (-1)^n cos(pi (phi' - n) - pi/4), argument in [-3pi/4, pi/4]
+  const float arg = j0_fma(phi - n, 3.14159265358979f, -0.785398163397448f);
+  const float v = (r * f0) * j0_cos(arg);
   return j0_bits_float(j0_float_bits(v) ^ (j0_float_bits(shifted) << 31));
 }
 

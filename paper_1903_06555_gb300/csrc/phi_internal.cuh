@@ -8,7 +8,7 @@
 //   perm[n_kept]        caller index of each sorted record, bit 31 = folded;
 //   omn_pix[N*N]        1 - n(l, m) per pixel (FP64, for the chirp phase);
 //   corr_pix[N*N]       1 / (g(du |l|) n(l, m)) per pixel (precision T);
-//   node tables         per admissible panel count P: 1 - n(r_j) (FP64) and
+//   node tables         per panel count P = 1..192: 1 - n(r_j) (FP64) and
 //                       w 2 pi h g(r_j) r_j (T, Kronrod and Kronrod-minus-
 //                       Gauss weights w) at the 15 P Gauss-Kronrod nodes;
 //   tap order           per even support J_w, its J_w^2 taps sorted by
@@ -31,22 +31,17 @@ namespace phi {
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr float kPiF = 3.14159265358979323846f;
 
-// Admissible panel counts: 1, 2, 3, 4, 6, 8, 12, ... (closed under doubling).
-constexpr int kNumPanelCounts = 16;  // up to 192 panels
-__host__ __device__ inline int panel_count_at(int i) {
-  if (i <= 0) return 1;
-  int e = (i - 1) / 2;
-  return ((i - 1) % 2 == 0 ? 2 : 3) << e;
+// Panel counts 1..kMaxPanels; the node tables hold every partition
+// (panel count P at offset 15 P (P - 1) / 2).
+constexpr int kMaxPanels = 192;
+__host__ __device__ inline int64_t panel_table_offset(int npan) {
+  return 15 * static_cast<int64_t>(npan) * (npan - 1) / 2;
 }
-__host__ __device__ inline int panel_count_index_for(float want) {
-  int i = 0;
-  while (i < kNumPanelCounts - 1 && panel_count_at(i) < want) ++i;
-  return i;
-}
-__host__ __device__ inline int64_t panel_table_offset(int i) {
-  int64_t off = 0;
-  for (int k = 0; k < i; ++k) off += 15 * panel_count_at(k);
-  return off;
+__host__ __device__ inline int panel_count_for(float want) {
+  // want may be NaN or huge: clamp without relying on the conversion
+  if (!(want > 1.0f)) return 1;
+  if (want >= static_cast<float>(kMaxPanels)) return kMaxPanels;
+  return static_cast<int>(ceilf(want));
 }
 
 // Panels evaluated per batch out of the per-warp shared node buffer.

@@ -139,13 +139,9 @@ __global__ void node_table_kernel(double R, double du, double a, double beta, do
                                   T* hk, T* hd, int64_t total) {
   int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (j >= total) return;
-  int i = 0;
-  int64_t off = 0;
-  while (i < kNumPanelCounts - 1 && off + 15 * panel_count_at(i) <= j) {
-    off += 15 * panel_count_at(i);
-    ++i;
-  }
-  int npan = panel_count_at(i);
+  int npan = 1;
+  while (npan < kMaxPanels && panel_table_offset(npan + 1) <= j) ++npan;
+  const int64_t off = panel_table_offset(npan);
   int64_t local = j - off;
   int p = static_cast<int>(local / 15);
   int k = static_cast<int>(local % 15);
@@ -174,7 +170,7 @@ __global__ void pixel_table_kernel(int N, double dl, double du, double a, double
 }
 
 int launch_node_tables(Plan& p, cudaStream_t s) {
-  int64_t total = panel_table_offset(kNumPanelCounts);
+  int64_t total = panel_table_offset(kMaxPanels + 1);
   int blocks = static_cast<int>((total + 255) / 256);
   double a = 0.5 * p.d.support;
   if (p.d.precision == PHI_F64)
@@ -271,9 +267,9 @@ __global__ void finish_kernel(const C* __restrict__ grid, const double* __restri
 // Build the weighted integrand values for panels [p0, p0 + np) of the
 // npan-panel partition: h(r_j) e^{2 pi i dw (1 - n(r_j))}, phase argument in FP64.
 template <typename T>
-__device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q, int pidx, int p0,
+__device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q, int npan, int p0,
                                             int np, double dw, int lane) {
-  const int64_t off = panel_table_offset(pidx) + 15 * (int64_t)p0;
+  const int64_t off = panel_table_offset(npan) + 15 * (int64_t)p0;
   const double* omn = q.node_omn + off;
   const T* hk = static_cast<const T*>(q.node_hk) + off;
   const T* hd = static_cast<const T*>(q.node_hd) + off;
@@ -301,7 +297,7 @@ __device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np
     const T a = Bh * static_cast<T>(2 * (p0 + p) + 1);
     const NodeVal<T>* hp = sh + 15 * p;
     T dr = 0, di = 0;
-#pragma unroll 5
+#pragma unroll
     for (int j = 0; j < 15; ++j) {
       const T u = fma(Bh, gk_node_c(T(0), j), a);
       const T J = j0_hc(u);
@@ -315,55 +311,51 @@ __device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np
   }
 }
 
-__device__ __forceinline__ int next_panel_index(int pidx) { return pidx == 0 ? 1 : pidx + 2; }
-
 // Evaluate [GC](rho, dw) for one tap per lane (inactive lanes compute a
-// harmless dummy) with the panel-count index pidx, refining the whole chunk
-// while any active tap misses the tolerance.  `built` (the panel-count index
-// whose nodes are resident in sh, or -1) is warp-uniform and updated.
+// harmless dummy) on npan panels, doubling the panels for the whole chunk
+// while any active tap misses the tolerance.  `built` (the panel count whose
+// nodes are resident in sh, or 0) is warp-uniform and updated.
 template <typename T, typename C>
 __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active, double dw,
-                        int pidx, int& built, bool& ok, int lane, unsigned long long& nodes) {
+                        int npan, int& built, bool& ok, int lane, unsigned long long& nodes) {
   int refine = 0;
   while (true) {
-    const int npan = panel_count_at(pidx);
     nodes += active ? 15ull * npan : 0ull;
     const T Bh = static_cast<T>(q.R / npan) * rho;   // 2 rho (R / (2 npan)), R/npan in FP64
     T kr = 0, ki = 0, err = 0;
     if (npan <= kPanelBatch) {
-      if (built != pidx) {
+      if (built != npan) {
         __syncwarp();
-        build_nodes<T>(sh, q, pidx, 0, npan, dw, lane);
+        build_nodes<T>(sh, q, npan, 0, npan, dw, lane);
         __syncwarp();
-        built = pidx;
+        built = npan;
       }
       eval_panels<T>(sh, 0, npan, Bh, kr, ki, err);
     } else {
       for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
         const int nb = min(kPanelBatch, npan - p0);
         __syncwarp();
-        build_nodes<T>(sh, q, pidx, p0, nb, dw, lane);
+        build_nodes<T>(sh, q, npan, p0, nb, dw, lane);
         __syncwarp();
         eval_panels<T>(sh, p0, nb, Bh, kr, ki, err);
       }
-      built = -1;
+      built = 0;
     }
     // err and |K| are both formed without cancellation (err from the
     // Kronrod-minus-Gauss weights), so the test runs in T.
     const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * sqrt(kr * kr + ki * ki));
     ok = (!active) || err <= lim;
     const bool any_bad = __any_sync(0xffffffffu, !ok);
-    const int nxt = next_panel_index(pidx);
-    if (!any_bad || refine >= q.max_refine || nxt >= kNumPanelCounts) return cmake<C>(kr, ki);
+    if (!any_bad || refine >= q.max_refine || 2 * npan > kMaxPanels) return cmake<C>(kr, ki);
     ++refine;
-    pidx = nxt;
+    npan *= 2;
   }
 }
 
 // Panels for the chunk: integrand cycles over [0, R] bounded by
 // R (rho_max + |dw| chirp_coeff), at inv_cycles panels per cycle.
-__device__ __forceinline__ int initial_panel_index(const QuadParams& q, float rho_max, float adw) {
-  return panel_count_index_for(q.Rf * fmaf(adw, q.chirp_coeff, rho_max) * q.inv_cycles);
+__device__ __forceinline__ int initial_panels(const QuadParams& q, float rho_max, float adw) {
+  return panel_count_for(q.Rf * fmaf(adw, q.chirp_coeff, rho_max) * q.inv_cycles);
 }
 
 // One warp per visibility, visibilities taken from a work queue.  Taps are
@@ -394,7 +386,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
     const T fu = r.fu, fv = r.fv;
     const uint16_t* order = q.tap_order + q.tap_off[half - 1];
     const float adw = static_cast<float>(fabs(r.dw));
-    int built = -1;
+    int built = 0;
     const uint32_t pm = perm[i];
     C yv = cmake<C>(0.0, 0.0);
     if (kGrid) {
@@ -416,9 +408,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
       T rmax = active ? rho : T(0);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-      const int pidx = initial_panel_index(q, static_cast<float>(rmax), adw);
+      const int npan = initial_panels(q, static_cast<float>(rmax), adw);
       bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, pidx, built, ok, lane, my_nodes);
+      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, built, ok, lane, my_nodes);
       if (active) {
         ++my_taps;
         if (!ok) ++my_bad;
@@ -477,12 +469,12 @@ __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__
   for (int64_t i = blockIdx.x * wpb + warp; i < n; i += (int64_t)gridDim.x * wpb) {
     const T rho = static_cast<T>(rho_in[i]);
     const double dw = dw_in[i];
-    int built = -1;
+    int built = 0;
     bool ok = true;
     unsigned long long nodes = 0;
     const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw,
-                                 initial_panel_index(q, static_cast<float>(rho),
-                                                     static_cast<float>(fabs(dw))),
+                                 initial_panels(q, static_cast<float>(rho),
+                                                static_cast<float>(fabs(dw))),
                                  built, ok, lane, nodes);
     if (lane == 0) {
       out[i] = K;

@@ -351,7 +351,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   const double tol = std::min(d.quad_rel_tol, d.quad_abs_tol);
   p.cycles_per_panel = d.cycles_per_panel > 0.0
                            ? d.cycles_per_panel
-                           : std::min(2.0, std::max(0.25, 1.5 * std::pow(tol / 1e-6, 1.0 / 14.0)));
+                           : std::min(2.5, std::max(0.25, 1.75 * std::pow(tol / 1e-6, 1.0 / 11.0)));
 
   int dev = 0;
   PHI_CUDA_TRY(cudaGetDevice(&dev));
@@ -500,7 +500,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
 
   // --- tables, grid, FFT plan
   const size_t tsize = f64 ? sizeof(double) : sizeof(float);
-  const int64_t nodes = panel_table_offset(kNumPanelCounts);
+  const int64_t nodes = panel_table_offset(kMaxPanels + 1);
   PHI_CUDA_TRY(owned_alloc(p, &p.node_omn, nodes));
   PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.node_hk), tsize * nodes));
   PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.node_hd), tsize * nodes));
