@@ -204,6 +204,55 @@ int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, void* stream
 int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, int64_t n,
                 void* k_dev, int64_t* n_unconverged, void* stream);
 
+/*
+ * Allocation-free kernel evaluation (no counterpart in the paper).
+ *
+ * For callers that must not allocate device memory once they are running:
+ * a host application whose device memory is owned by another allocator
+ * (for example a framework's caching pool that has reserved the GPU), or a
+ * real-time imaging pipeline in which cudaMalloc's implicit device-wide
+ * synchronisation would stall the streams that are already working.
+ * phi_wkernel_noalloc evaluates [GC](rho_i, dw_i) like phi_wkernel, with the
+ * same device routine, but without a plan and without allocating: its
+ * scratch (the quadrature node tables and one counter) lives in a fixed
+ * file-scope device array of PHI_WKERNEL_NOALLOC_SCRATCH_BYTES (about 732
+ * KiB), which every GPU that loads the library holds until the process
+ * exits.  The caller passes the inputs and outputs.
+ *
+ *   params:  geometry and quadrature settings (below); max_panels must be in
+ *            1..PHI_WKERNEL_NOALLOC_MAX_PANELS, otherwise PHI_ERR_ARG and
+ *            nothing runs.  Points that would need more panels are evaluated
+ *            with max_panels and counted as unconverged.
+ *   rho_dev, dw_dev, n, k_dev, n_unconverged, stream: as for phi_wkernel.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call rebuilds the node tables for its own parameters and
+ * zeroes the counter, so a call does not depend on the one before it, but
+ * all calls on a device share the one array: calls whose work overlaps on
+ * the GPU (different streams, or host threads racing) race on it and must be
+ * serialised by the caller.
+ */
+#define PHI_WKERNEL_NOALLOC_MAX_PANELS 64
+#define PHI_WKERNEL_NOALLOC_SCRATCH_BYTES (256 + 3 * 8 * (15 * 64 * 65 / 2))
+
+typedef struct {
+  double du;                /* grid spacing in wavelengths (phi_plan_info du)   */
+  double window_radius;     /* R = alpha / 2 in r = du * l units                */
+  double kb_beta;           /* Kaiser-Bessel shape, > 0                          */
+  double quad_rel_tol;      /* > 0                                               */
+  double quad_abs_tol;      /* > 0                                               */
+  double cycles_per_panel;  /* a-priori panel width in integrand cycles, > 0    */
+  int32_t support;          /* J, even, 2..64                                    */
+  int32_t max_refine;       /* panel-count doublings allowed, 0..8               */
+  int32_t max_panels;       /* 1..PHI_WKERNEL_NOALLOC_MAX_PANELS                 */
+  int32_t precision;        /* PHI_F32 or PHI_F64 (output element type)          */
+} phi_wkernel_params;
+
+int phi_wkernel_noalloc(const phi_wkernel_params* params, const double* rho_dev,
+                        const double* dw_dev, int64_t n, void* k_dev, int64_t* n_unconverged,
+                        void* stream);
+
 /* Static string naming a status code. */
 const char* phi_error_string(int status);
 

@@ -80,6 +80,24 @@ class PlanSummary(ctypes.Structure):
     ]
 
 
+class WKernelParams(ctypes.Structure):
+    """Mirror of phi_wkernel_params (include/phi.h)."""
+    _fields_ = [
+        ("du", ctypes.c_double),
+        ("window_radius", ctypes.c_double),
+        ("kb_beta", ctypes.c_double),
+        ("quad_rel_tol", ctypes.c_double),
+        ("quad_abs_tol", ctypes.c_double),
+        ("cycles_per_panel", ctypes.c_double),
+        ("support", ctypes.c_int32),
+        ("max_refine", ctypes.c_int32),
+        ("max_panels", ctypes.c_int32),
+        ("precision", ctypes.c_int32),
+    ]
+
+
+WKERNEL_NOALLOC_MAX_PANELS = 64
+
 _LIB = None
 _LOCK = threading.Lock()
 _vp = ctypes.c_void_p
@@ -112,6 +130,8 @@ def lib():
             L.phi_degrid.argtypes = [_vp, _vp, _vp, _vp]
             L.phi_grid.argtypes = [_vp, _vp, _vp, _vp]
             L.phi_wkernel.argtypes = [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(_i64), _vp]
+            L.phi_wkernel_noalloc.argtypes = [ctypes.POINTER(WKernelParams), _vp, _vp, _i64, _vp,
+                                              ctypes.POINTER(_i64), _vp]
             L.phi_error_string.argtypes = [ctypes.c_int]
             L.phi_error_string.restype = ctypes.c_char_p
             _LIB = L
@@ -288,4 +308,29 @@ class Plan:
         return {STAGES[i]: (ms[i], int(n[i])) for i in range(NUM_STAGES)}
 
 
-__all__ = ["Plan", "PlanDesc", "PlanSummary", "PhiError", "default_desc", "lib", "lib_path"]
+def wkernel_noalloc(params: WKernelParams, rho, dw, stream=None):
+    """[GC](rho, dw) without a plan and without any device allocation inside
+    the library (its scratch is a fixed array in the library itself), for
+    callers that must not allocate device memory while running.  rho and dw
+    must already be float64 CUDA tensors of equal size; returns (complex
+    tensor, number of points above tolerance).  The output tensor is
+    allocated here by PyTorch; callers that cannot allocate pass their own
+    buffer to the C entry point directly."""
+    if rho.dtype != torch.float64 or dw.dtype != torch.float64 or rho.shape != dw.shape:
+        raise ValueError("rho and dw must be float64 tensors of the same shape")
+    if not rho.is_cuda or not dw.is_cuda:
+        raise ValueError("rho and dw must be on the GPU")
+    rho = rho.contiguous().ravel()
+    dw = dw.contiguous().ravel()
+    cd = torch.complex128 if params.precision == PHI_F64 else torch.complex64
+    k = torch.empty(rho.numel(), dtype=cd, device=rho.device)
+    bad = _i64(0)
+    _check(lib().phi_wkernel_noalloc(ctypes.byref(params), ctypes.c_void_p(rho.data_ptr()),
+                                     ctypes.c_void_p(dw.data_ptr()), rho.numel(),
+                                     ctypes.c_void_p(k.data_ptr()), ctypes.byref(bad),
+                                     _stream(stream)), "phi_wkernel_noalloc")
+    return k, int(bad.value)
+
+
+__all__ = ["Plan", "PlanDesc", "PlanSummary", "PhiError", "WKernelParams", "default_desc", "lib",
+           "lib_path", "wkernel_noalloc"]

@@ -20,6 +20,8 @@
 // transpose pair exactly.
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "bessel_j0.cuh"
 #include "phi_internal.cuh"
 
@@ -708,4 +710,186 @@ extern "C" int phi_plan_timings(phi_plan_t plan, double* ms, int64_t* launches, 
     }
   }
   return PHI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free kernel evaluation (phi_wkernel_noalloc)
+//
+// Callers that cannot allocate device memory while running get the plan-free
+// evaluator below.  Its scratch -- node tables for panel counts 1..64 and the
+// unconverged counter -- is this file-scope array rather than plan memory.
+// The array's name is only a host-side stand-in for the device object; the
+// kernels receive the device address that cudaGetSymbolAddress returns.
+// ---------------------------------------------------------------------------
+namespace phi {
+namespace {
+
+constexpr int kNoAllocMaxPanels = PHI_WKERNEL_NOALLOC_MAX_PANELS;
+constexpr int64_t kNoAllocNodes = 15LL * kNoAllocMaxPanels * (kNoAllocMaxPanels + 1) / 2;
+constexpr size_t kNoAllocBytes = PHI_WKERNEL_NOALLOC_SCRATCH_BYTES;
+static_assert(kNoAllocBytes == 256 + 3 * 8 * kNoAllocNodes, "scratch layout");
+
+// [0, 256): counter; then omn (FP64), hk, hd (8 bytes per node reserved each).
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once
+// per device).
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return PHI_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      (void)cudaGetLastError();
+      return PHI_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = ptr;
+  }
+  *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+  return PHI_OK;
+}
+
+// eval_chunk with the panel count capped at the scratch tables' maximum.
+template <typename T, typename C>
+__device__ C eval_chunk_capped(NodeVal<T>* sh, const QuadParams& q, T rho, bool active, double dw,
+                               int npan, int max_panels, int& built, bool& ok, int lane) {
+  npan = min(npan, max_panels);
+  int refine = 0;
+  while (true) {
+    const T Bh = static_cast<T>(q.R / npan) * rho;
+    T kr = 0, ki = 0, err = 0;
+    if (npan <= kPanelBatch) {
+      if (built != npan) {
+        __syncwarp();
+        build_nodes<T>(sh, q, npan, 0, npan, dw, lane);
+        __syncwarp();
+        built = npan;
+      }
+      eval_panels<T>(sh, 0, npan, Bh, kr, ki, err);
+    } else {
+      for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
+        const int nb = min(kPanelBatch, npan - p0);
+        __syncwarp();
+        build_nodes<T>(sh, q, npan, p0, nb, dw, lane);
+        __syncwarp();
+        eval_panels<T>(sh, p0, nb, Bh, kr, ki, err);
+      }
+      built = 0;
+    }
+    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * sqrt(kr * kr + ki * ki));
+    ok = (!active) || err <= lim;
+    const bool any_bad = __any_sync(0xffffffffu, !ok);
+    if (!any_bad || refine >= q.max_refine || 2 * npan > max_panels) return cmake<C>(kr, ki);
+    ++refine;
+    npan *= 2;
+  }
+}
+
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) wkernel_noalloc_kernel(const double* __restrict__ rho_in,
+                                                              const double* __restrict__ dw_in,
+                                                              int64_t n, C* __restrict__ out,
+                                                              QuadParams q, int max_panels,
+                                                              unsigned long long* bad) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
+  const int64_t wpb = blockDim.x >> 5;
+  for (int64_t i = blockIdx.x * wpb + warp; i < n; i += (int64_t)gridDim.x * wpb) {
+    const T rho = static_cast<T>(rho_in[i]);
+    const double dw = dw_in[i];
+    int built = 0;
+    bool ok = true;
+    const C K = eval_chunk_capped<T, C>(
+        sh, q, rho, lane == 0, dw,
+        initial_panels(q, static_cast<float>(rho), static_cast<float>(fabs(dw))), max_panels,
+        built, ok, lane);
+    if (lane == 0) {
+      out[i] = K;
+      if (!ok) atomicAdd(bad, 1ULL);
+    }
+  }
+}
+
+template <typename T, typename C>
+int run_wkernel_noalloc(const phi_wkernel_params& prm, const double* rho, const double* dw,
+                        int64_t n, C* out, int64_t* n_bad, cudaStream_t s) {
+  unsigned char* base = nullptr;
+  int st = noalloc_scratch(&base);
+  if (st != PHI_OK) return st;
+  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
+  PHI_CUDA_TRY(cudaFuncSetAttribute(wkernel_noalloc_kernel<T, C>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  unsigned long long* bad = reinterpret_cast<unsigned long long*>(base);
+  double* omn = reinterpret_cast<double*>(base + 256);
+  T* hk = reinterpret_cast<T*>(base + 256 + 8 * kNoAllocNodes);
+  T* hd = reinterpret_cast<T*>(base + 256 + 16 * kNoAllocNodes);
+  const int64_t nodes = panel_table_offset(prm.max_panels + 1);
+  const double l_win = prm.window_radius / prm.du;
+  const double n_win = sqrt(1.0 - l_win * l_win);
+  QuadParams q;
+  q.R = prm.window_radius;
+  q.Rf = static_cast<float>(prm.window_radius);
+  q.chirp_coeff = static_cast<float>(l_win / (n_win * prm.du));
+  q.inv_cycles = static_cast<float>(1.0 / prm.cycles_per_panel);
+  q.tol_rel = static_cast<float>(prm.quad_rel_tol);
+  q.tol_abs = static_cast<float>(prm.quad_abs_tol);
+  q.max_refine = prm.max_refine;
+  q.npad = 0;
+  q.node_omn = omn;
+  q.node_hk = hk;
+  q.node_hd = hd;
+  q.tap_order = nullptr;
+  q.tap_off = nullptr;
+  // the counter keeps the previous call's value: clear it first
+  PHI_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), s));
+  node_table_kernel<T><<<static_cast<int>((nodes + 255) / 256), 256, 0, s>>>(
+      prm.window_radius, prm.du, 0.5 * prm.support, prm.kb_beta, omn, hk, hd, nodes);
+  PHI_CUDA_TRY(cudaGetLastError());
+  if (n > 0) {
+    const int64_t want = (n + 7) / 8;
+    const int blocks = static_cast<int>(want < 65535 ? want : 65535);
+    wkernel_noalloc_kernel<T, C><<<blocks, kVisThreads, smem, s>>>(rho, dw, n, out, q,
+                                                                   prm.max_panels, bad);
+    PHI_CUDA_TRY(cudaGetLastError());
+  }
+  if (n_bad) {
+    unsigned long long h = 0;
+    PHI_CUDA_TRY(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+    *n_bad = static_cast<int64_t>(h);
+  }
+  return PHI_OK;
+}
+
+}  // namespace
+}  // namespace phi
+
+extern "C" int phi_wkernel_noalloc(const phi_wkernel_params* params, const double* rho_dev,
+                                   const double* dw_dev, int64_t n, void* k_dev,
+                                   int64_t* n_unconverged, void* stream) {
+  if (!params || n < 0 || (n > 0 && (!rho_dev || !dw_dev || !k_dev))) return PHI_ERR_ARG;
+  const phi_wkernel_params& p = *params;
+  if (p.max_panels < 1 || p.max_panels > PHI_WKERNEL_NOALLOC_MAX_PANELS) return PHI_ERR_ARG;
+  if (p.support < 2 || p.support > 64 || p.support % 2) return PHI_ERR_ARG;
+  if (!(p.du > 0.0) || !(p.window_radius > 0.0) || !(p.kb_beta > 0.0)) return PHI_ERR_ARG;
+  if (!(p.quad_rel_tol > 0.0) || !(p.quad_abs_tol > 0.0) || !(p.cycles_per_panel > 0.0))
+    return PHI_ERR_ARG;
+  if (p.max_refine < 0 || p.max_refine > 8) return PHI_ERR_ARG;
+  if (p.precision != PHI_F32 && p.precision != PHI_F64) return PHI_ERR_ARG;
+  if (p.window_radius / p.du >= 1.0) return PHI_ERR_HORIZON;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.precision == PHI_F64)
+    return phi::run_wkernel_noalloc<double, double2>(p, rho_dev, dw_dev, n,
+                                                     static_cast<double2*>(k_dev), n_unconverged, s);
+  return phi::run_wkernel_noalloc<float, float2>(p, rho_dev, dw_dev, n,
+                                                 static_cast<float2*>(k_dev), n_unconverged, s);
 }
