@@ -149,6 +149,34 @@ def measured_peaks():
     return {}
 
 
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("phi_ops.cu", "bessel_j0.cuh", "phi_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1903_06555_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(stage):
+    """DRAM bytes per launch of the fused kernel from the committed ncu launch
+    list, or None when the kernel sources changed since it was taken."""
+    p = os.path.join(ROOT, "profiles", "vis_kernel_mwa-2048-8stack_launches.md")
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().split(":")[0] in (
+                "kernel_source_sha256", "traffic_bytes_per_launch_degrid",
+                "traffic_bytes_per_launch_grid"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    v = vals.get(f"traffic_bytes_per_launch_{stage}")
+    return float(v) if v else None
+
+
 def load_oracle_counts():
     p = os.path.join(ROOT, "tests", "golden", "mwa_oracle_evals.json")
     with open(p) as f:
@@ -336,7 +364,7 @@ def run_ours(args, ws, rank, local):
                        "oracle_tap_nodes_per_vis_tol1e-6": evals_per_vis},
         "roofline": {"bound": "alu", "kernel": f"vis_kernel ({dom})", "achieved": achieved,
                      "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
-                     "traffic": None,
+                     "traffic": profiled_traffic(dom),
                      "peak_note": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
                                   f"{sm_mhz:.0f} MHz (recipe unit counts, max clock)",
                      "work_note": f"{FLOPS_PER_TAP_NODE:.0f} flops per tap-node x oracle tap-nodes "
