@@ -135,6 +135,24 @@ int phi_plan_desc_default(phi_plan_desc* desc);
 int phi_plan_create(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
                     const double* weights_dev, int64_t n_vis, void* stream);
 
+/*
+ * As phi_plan_create, but with the w-stack centres given instead of found by
+ * Algorithm 1: each visibility joins its nearest centre by (wbar_k - w)^2
+ * (lowest index on ties) and wbar_k = centres[k].  stack_jw, when non-NULL,
+ * replaces the support rule with these per-stack supports (even, 2 ..
+ * max_support; PHI_SUPPORT_STACK only), so that a plan over part of an
+ * observation reproduces the operator of the plan over all of it (take the
+ * centres and supports from phi_plan_info) for every visibility whose
+ * nearest final centre is the stack Algorithm 1's last sweep gave it (all
+ * but those within the last centre shift of a stack boundary; the plan built
+ * here assigns by nearest centre).  centres and stack_jw are host
+ * arrays of n_stacks entries.  PHI_ERR_ARG for non-finite centres or invalid
+ * supports.
+ */
+int phi_plan_create_fixed(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
+                          const double* weights_dev, int64_t n_vis, const double* centres,
+                          const int32_t* stack_jw, void* stream);
+
 /* Release the plan (after its last call has completed on its stream). */
 void phi_plan_destroy(phi_plan_t plan);
 

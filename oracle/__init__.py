@@ -376,24 +376,35 @@ def support(dw, geo: Geometry):
 
 def make_plan(uvw, geo: Geometry, n_stacks=1, conj_fold=False, weights=None,
               kmeans_max_iter=100, kmeans_tol=1e-3, max_support=64,
-              support_rule=SUPPORT_STACK) -> OraclePlan:
+              support_rule=SUPPORT_STACK, centres=None, stack_jw=None) -> OraclePlan:
     """Fold, Algorithm 1, grid coordinates u/du, drop visibilities whose own
     (u, v) lies outside the padded grid [-Npad/2, Npad/2) (their taps would
     alias; the taps of every kept visibility wrap circularly, G being a
     circular convolution), then the support: per stack from the largest |dw|
-    of its kept visibilities (SUPPORT_STACK) or per visibility."""
+    of its kept visibilities (SUPPORT_STACK) or per visibility.
+
+    With `centres`, Algorithm 1 is replaced by one assignment of every
+    visibility to its nearest given centre (lowest index on ties), and the
+    centres are kept; with `stack_jw` the per-stack supports are given."""
     uvw = np.asarray(uvw, dtype=np.float64)
     if conj_fold:
         uvw, flag = fold(uvw)
     else:
         flag = np.zeros(uvw.shape[0], bool)
-    st, c, it = kmeans(uvw[:, 2], n_stacks, kmeans_max_iter, kmeans_tol)
+    if centres is None:
+        st, c, it = kmeans(uvw[:, 2], n_stacks, kmeans_max_iter, kmeans_tol)
+    else:
+        c = np.asarray(centres, np.float64)
+        st = np.argmin((c[None, :] - uvw[:, 2:3]) ** 2, axis=1).astype(np.int32)
+        it = 0
     dw = uvw[:, 2] - c[st]
     upix = uvw[:, 0] / geo.du
     vpix = uvw[:, 1] / geo.du
     h = geo.Npad // 2
     dropped = (upix < -h) | (upix >= h) | (vpix < -h) | (vpix >= h)
-    if support_rule == SUPPORT_VIS:
+    if stack_jw is not None:
+        jw = np.asarray(stack_jw, np.int32)[st]
+    elif support_rule == SUPPORT_VIS:
         jw = support(dw, geo)
     else:
         jw = np.zeros(dw.size, np.int32)

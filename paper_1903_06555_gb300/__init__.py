@@ -119,6 +119,9 @@ def lib():
             L.phi_plan_desc_default.argtypes = [ctypes.POINTER(PlanDesc)]
             L.phi_plan_create.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(PlanDesc), _vp, _vp,
                                           _i64, _vp]
+            L.phi_plan_create_fixed.argtypes = [ctypes.POINTER(_vp), ctypes.POINTER(PlanDesc), _vp,
+                                                _vp, _i64, ctypes.POINTER(ctypes.c_double),
+                                                ctypes.POINTER(ctypes.c_int32), _vp]
             L.phi_plan_destroy.argtypes = [_vp]
             L.phi_plan_destroy.restype = None
             L.phi_plan_info.argtypes = [_vp, ctypes.POINTER(PlanSummary), _vp, _vp, _vp]
@@ -179,7 +182,7 @@ class Plan:
     support_rule='stack'|'vis', quad_rel_tol, ...).
     """
 
-    def __init__(self, uvw, weights=None, stream=None, **desc):
+    def __init__(self, uvw, weights=None, stream=None, centres=None, stack_jw=None, **desc):
         self.desc = default_desc(**desc)
         dev = torch.device("cuda", torch.cuda.current_device())
         uvw = torch.as_tensor(uvw, dtype=torch.float64).to(dev).contiguous()
@@ -195,10 +198,20 @@ class Plan:
         self.real_dtype = torch.float64 if self.desc.precision == PHI_F64 else torch.float32
         self.complex_dtype = torch.complex128 if self.desc.precision == PHI_F64 else torch.complex64
         h = ctypes.c_void_p()
-        _check(lib().phi_plan_create(ctypes.byref(h), ctypes.byref(self.desc),
-                                     ctypes.c_void_p(uvw.data_ptr()),
-                                     ctypes.c_void_p(w.data_ptr() if w is not None else 0),
-                                     self.n_vis, _stream(stream)), "phi_plan_create")
+        wptr = ctypes.c_void_p(w.data_ptr() if w is not None else 0)
+        if centres is None:
+            if stack_jw is not None:
+                raise ValueError("stack_jw needs centres")
+            _check(lib().phi_plan_create(ctypes.byref(h), ctypes.byref(self.desc),
+                                         ctypes.c_void_p(uvw.data_ptr()), wptr, self.n_vis,
+                                         _stream(stream)), "phi_plan_create")
+        else:
+            K = int(self.desc.n_stacks)
+            c = (ctypes.c_double * K)(*[float(v) for v in centres])
+            j = None if stack_jw is None else (ctypes.c_int32 * K)(*[int(v) for v in stack_jw])
+            _check(lib().phi_plan_create_fixed(ctypes.byref(h), ctypes.byref(self.desc),
+                                               ctypes.c_void_p(uvw.data_ptr()), wptr, self.n_vis,
+                                               c, j, _stream(stream)), "phi_plan_create_fixed")
         self._h = h
         self.image_n = int(self.desc.image_n)
 

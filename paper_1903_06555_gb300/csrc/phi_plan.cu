@@ -324,7 +324,8 @@ int build_tap_order(Plan& p, int jmax, cudaStream_t s) {
   return PHI_OK;
 }
 
-int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStream_t s) {
+int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStream_t s,
+          const double* fixed_centres, const int32_t* fixed_jw) {
   const phi_plan_desc& d = p.d;
   p.N = d.image_n;
   p.npad = static_cast<int>(std::lround(d.oversample * d.image_n));
@@ -396,16 +397,24 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
     wmax = *std::max_element(hmax.begin(), hmax.end());
   }
 
-  // --- Algorithm 1
+  // --- Algorithm 1 (or one nearest-centre assignment to given centres)
   std::vector<double> c(K);
   for (int q = 0; q < K; ++q)
-    c[q] = (K == 1) ? 0.5 * (wmin + wmax) : wmin + q * (wmax - wmin) / (K - 1);
+    c[q] = fixed_centres ? fixed_centres[q]
+                         : (K == 1) ? 0.5 * (wmin + wmax) : wmin + q * (wmax - wmin) / (K - 1);
   double eps = (wmax - wmin) / K;
   if (!(eps > 0.0)) eps = 1.0;
   PHI_CUDA_TRY(cudaMemcpyAsync(centres, c.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
   std::vector<double> hupd(2 * K + 1);
   p.kmeans_sweeps = 0;
-  if (M > 0) {
+  if (M > 0 && fixed_centres) {
+    const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
+    const size_t smem = sizeof(double) * (K + 2 * (kPlanThreads / 32) * K);
+    kmeans_sweep_kernel<<<nblk, kPlanThreads, smem, s>>>(w_fold, M, chunk, centres, K, stack, psum,
+                                                         pcnt);
+    PHI_CUDA_TRY(cudaGetLastError());
+    for (int q = 0; q < K; ++q) p.wbar[q] = c[q];
+  } else if (M > 0) {
     const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
     const size_t smem = sizeof(double) * (K + 2 * (kPlanThreads / 32) * K);
     while (p.kmeans_sweeps < d.kmeans_max_iter) {
@@ -455,6 +464,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
     unsigned long long bits = hstat[q];
     std::memcpy(&maxabs, &bits, sizeof(double));
     p.stack_jw[q] = hstat[K + q] ? d.support + 2 * static_cast<int32_t>(std::ceil(maxabs * p.c_support)) : 0;
+    if (fixed_jw && hstat[K + q]) p.stack_jw[q] = fixed_jw[q];
   }
   p.stack_off[K] = p.n_kept;
   p.n_dropped = M - p.n_kept;
@@ -547,17 +557,30 @@ extern "C" int phi_plan_desc_default(phi_plan_desc* d) {
   return PHI_OK;
 }
 
-extern "C" int phi_plan_create(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
-                               const double* weights_dev, int64_t n_vis, void* stream) {
+namespace {
+
+int create(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
+           const double* weights_dev, int64_t n_vis, const double* centres,
+           const int32_t* stack_jw, void* stream) {
   if (!out || !desc) return PHI_ERR_ARG;
   *out = nullptr;
   int st = phi::validate(*desc, n_vis);
   if (st != PHI_OK) return st;
   if (n_vis > 0 && !uvw_dev) return PHI_ERR_ARG;
+  if (centres) {
+    for (int q = 0; q < desc->n_stacks; ++q)
+      if (!std::isfinite(centres[q])) return PHI_ERR_ARG;
+  }
+  if (stack_jw) {
+    if (!centres || desc->support_rule != PHI_SUPPORT_STACK) return PHI_ERR_ARG;
+    for (int q = 0; q < desc->n_stacks; ++q)
+      if (stack_jw[q] < 2 || stack_jw[q] % 2 || stack_jw[q] > desc->max_support) return PHI_ERR_ARG;
+  }
   phi_plan* p = new (std::nothrow) phi_plan();
   if (!p) return PHI_ERR_OOM;
   p->d = *desc;
-  st = phi::build(*p, uvw_dev, weights_dev, n_vis, static_cast<cudaStream_t>(stream));
+  st = phi::build(*p, uvw_dev, weights_dev, n_vis, static_cast<cudaStream_t>(stream), centres,
+                  stack_jw);
   if (st != PHI_OK) {
     cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
     phi::free_plan(p);
@@ -566,6 +589,21 @@ extern "C" int phi_plan_create(phi_plan_t* out, const phi_plan_desc* desc, const
   }
   *out = p;
   return PHI_OK;
+}
+
+}  // namespace
+
+extern "C" int phi_plan_create(phi_plan_t* out, const phi_plan_desc* desc, const double* uvw_dev,
+                               const double* weights_dev, int64_t n_vis, void* stream) {
+  return create(out, desc, uvw_dev, weights_dev, n_vis, nullptr, nullptr, stream);
+}
+
+extern "C" int phi_plan_create_fixed(phi_plan_t* out, const phi_plan_desc* desc,
+                                     const double* uvw_dev, const double* weights_dev,
+                                     int64_t n_vis, const double* centres,
+                                     const int32_t* stack_jw, void* stream) {
+  if (!centres) return PHI_ERR_ARG;
+  return create(out, desc, uvw_dev, weights_dev, n_vis, centres, stack_jw, stream);
 }
 
 extern "C" void phi_plan_destroy(phi_plan_t plan) {
