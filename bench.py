@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="mwa", choices=["mwa", "serve"],
+                    help="mwa: the headline operator benchmark; serve: the serving stream")
+    ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-full-scale", type=int, default=1,
+                    help="append the 126.6M-visibility request to the serving stream")
     ap.add_argument("--support-rule", default="stack", choices=["stack", "vis"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -417,11 +422,105 @@ def run_e2e(phi, desc, uvw_np, x_np, steps, dev):
             "note": "includes plan build (fold, k-means, sort, tables, cuFFT plan)"}
 
 
+# ---------------------------------------------------------------------------- serving
+
+def serve_requests(n, seed=0, mmin=5e4, mmax=2e7, sizes=(512, 1024, 2048, 4096, 8192),
+                   precision="f32", cap=64):
+    """Synthetic serving stream: observations of log-uniform visibility
+    counts, image sizes log-uniform over powers of two, |w|max ~ U[50, 3000]
+    (fold on), K ~ U{1..64} raised by the client where the support would
+    exceed the cap."""
+    from paper_1903_06555_gb300 import serve as S
+    rng = np.random.default_rng(seed)
+    fov = math.radians(25.0)
+    c_sup = 0.5 * 2 * fov / math.sqrt(1 - (0.5 * 2 * fov) ** 2) * 2 * fov  # l_win/(n_win du), os 2
+    reqs = []
+    for i in range(n):
+        m = int(math.exp(rng.uniform(math.log(mmin), math.log(mmax))))
+        N = int(rng.choice(sizes))
+        wmax = float(rng.uniform(50, 3000))
+        k = int(rng.integers(1, 65))
+        k = min(126, max(k, int(math.ceil(1.6 * wmax * c_sup / (cap - 4)))))
+        n_times = -(-m // 8128)
+        uvw = W.uvw_earth_rotation(128, 3000.0, 150e6, -26.7, -37.2, -float(n_times) / 240,
+                                   float(n_times) / 240, n_times, wmax=wmax, seed=seed * 1000 + i)[:m]
+        desc = dict(image_n=N, fov_rad=fov, n_stacks=k, conj_fold=1, precision=precision,
+                    max_support=cap, quad_rel_tol=1e-12 if precision == "f64" else 1e-6,
+                    quad_abs_tol=1e-12 if precision == "f64" else 1e-6)
+        img = W.point_sources(N, 20, seed * 1000 + i)
+        reqs.append(S.Request(i, np.ascontiguousarray(uvw), desc, image=img,
+                              ops=("degrid", "grid")))
+    return reqs
+
+
+def poisson_arrivals(reqs, rate, seed=0):
+    t = 0.0
+    rng = np.random.default_rng(seed + 77)
+    for r in reqs:
+        t += rng.exponential(1.0 / rate)
+        r.arrival = t
+    return reqs
+
+
+def run_serve(args):
+    from paper_1903_06555_gb300 import serve as S
+    budget = 150 * 10 ** 9
+    # capacity probe: the headline operator rate sets the arrival rate
+    probe = serve_requests(6, seed=99, mmax=2e6)
+    with S.Server(budget, slots=4) as srv:
+        t0 = time.perf_counter()
+        srv.run_stream(probe, realtime=False)
+        probe_rate = sum(len(r.uvw) for r in probe) / (time.perf_counter() - t0)
+    reqs = serve_requests(args.serve_requests, seed=1)
+    mean_vis = float(np.mean([len(r.uvw) for r in reqs]))
+    rate = 0.8 * probe_rate / mean_vis
+    poisson_arrivals(reqs, rate)
+    if args.serve_full_scale:
+        from paper_1903_06555_gb300.serve import Request
+        n_times = -(-126_600_000 // 8128)
+        uvw = W.uvw_earth_rotation(128, 3000.0, 150e6, -26.7, -37.2, -n_times / 240,
+                                   n_times / 240, n_times, wmax=600.0, seed=5)[:126_600_000]
+        full = Request(10_000, np.ascontiguousarray(uvw),
+                       dict(image_n=8192, fov_rad=math.radians(25.0), n_stacks=64, conj_fold=1),
+                       image=W.point_sources(8192, 200, 5), ops=("degrid", "grid"),
+                       arrival=reqs[len(reqs) // 2].arrival)
+        reqs.append(full)
+    with S.Server(budget, slots=4) as srv:
+        res = srv.run_stream(reqs)
+        peak = srv.peak_bytes
+    summ = S.summarize(res)
+    full_res = [r for r in res if r.rid == 10_000]
+    # FP32 vs FP64 on the same reduced stream, back to back
+    cmp = {}
+    for prec in ("f32", "f64"):
+        small = poisson_arrivals(serve_requests(16, seed=7, mmin=5e4, mmax=4e5, sizes=(512, 1024),
+                                                precision=prec), rate=1000.0)
+        with S.Server(budget, slots=4) as srv:
+            r2 = srv.run_stream(small)
+        cmp[prec] = S.summarize(r2)
+    line = {"metric": "served w-corrected visibilities/s (degrid+grid per request), p50/p99 latency",
+            "value": summ.get("vis_per_s"), "unit": UNIT, "n_gpus": 1,
+            "workload": "serving: Poisson stream of %d observations (5e4-2e7 vis, 512^2-8192^2, "
+                        "|w|max 50-3000, K 1-64 raised to fit J_w <= 64) + 126.6M-vis 8192^2 request"
+                        % args.serve_requests,
+            "arrival_rate_per_s": rate, "probe_vis_per_s": probe_rate, "hbm_budget_bytes": budget,
+            "peak_admitted_bytes": peak, "summary": summ,
+            "full_scale": None if not full_res else {
+                "status": full_res[0].status, "error": full_res[0].error,
+                "latency_s": full_res[0].latency, "n_vis": full_res[0].n_vis,
+                "device_bytes": full_res[0].device_bytes},
+            "fp32_vs_fp64_reduced_stream": cmp}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "serve":
+        if rank == 0:
+            run_serve(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
