@@ -463,17 +463,23 @@ def poisson_arrivals(reqs, rate, seed=0):
 
 
 def run_serve(args):
+    """The serving workload: a closed-loop pass over requests drawn from the
+    stream's distribution measures capacity (kept visibilities/s); the
+    Poisson stream then arrives at 80% of it.  Requests whose support would
+    exceed the cap are retried by the engine with twice the stacks."""
     from paper_1903_06555_gb300 import serve as S
     budget = 150 * 10 ** 9
-    # capacity probe: the headline operator rate sets the arrival rate
-    probe = serve_requests(6, seed=99, mmax=2e6)
+    probe = serve_requests(24, seed=99)
+    for r in probe:
+        r.raise_stacks = True
     with S.Server(budget, slots=4) as srv:
-        t0 = time.perf_counter()
-        srv.run_stream(probe, realtime=False)
-        probe_rate = sum(len(r.uvw) for r in probe) / (time.perf_counter() - t0)
+        pres = srv.run_stream(probe, realtime=False)
+    cap = S.summarize(pres, t_first=0.0)
     reqs = serve_requests(args.serve_requests, seed=1)
-    mean_vis = float(np.mean([len(r.uvw) for r in reqs]))
-    rate = 0.8 * probe_rate / mean_vis
+    for r in reqs:
+        r.raise_stacks = True
+    mean_kept = cap["vis"] / max(cap["ok"], 1)
+    rate = 0.8 * cap["vis_per_s"] / mean_kept
     poisson_arrivals(reqs, rate)
     if args.serve_full_scale:
         from paper_1903_06555_gb300.serve import Request
@@ -483,32 +489,35 @@ def run_serve(args):
         full = Request(10_000, np.ascontiguousarray(uvw),
                        dict(image_n=8192, fov_rad=math.radians(25.0), n_stacks=64, conj_fold=1),
                        image=W.point_sources(8192, 200, 5), ops=("degrid", "grid"),
-                       arrival=reqs[len(reqs) // 2].arrival)
+                       arrival=reqs[len(reqs) // 2].arrival, raise_stacks=True)
         reqs.append(full)
     with S.Server(budget, slots=4) as srv:
         res = srv.run_stream(reqs)
         peak = srv.peak_bytes
     summ = S.summarize(res)
     full_res = [r for r in res if r.rid == 10_000]
+    raised = sum(1 for r, q in zip(res, reqs) if r.status == "ok" and r.n_stacks > q.desc["n_stacks"])
     # FP32 vs FP64 on the same reduced stream, back to back
     cmp = {}
     for prec in ("f32", "f64"):
         small = poisson_arrivals(serve_requests(16, seed=7, mmin=5e4, mmax=4e5, sizes=(512, 1024),
                                                 precision=prec), rate=1000.0)
+        for r in small:
+            r.raise_stacks = True
         with S.Server(budget, slots=4) as srv:
             r2 = srv.run_stream(small)
         cmp[prec] = S.summarize(r2)
     line = {"metric": "served w-corrected visibilities/s (degrid+grid per request), p50/p99 latency",
-            "value": summ.get("vis_per_s"), "unit": UNIT, "n_gpus": 1,
+            "value": summ.get("vis_per_s"), "unit": UNIT, "n_gpus": 1, "dtype": "f32",
             "workload": "serving: Poisson stream of %d observations (5e4-2e7 vis, 512^2-8192^2, "
                         "|w|max 50-3000, K 1-64 raised to fit J_w <= 64) + 126.6M-vis 8192^2 request"
                         % args.serve_requests,
-            "arrival_rate_per_s": rate, "probe_vis_per_s": probe_rate, "hbm_budget_bytes": budget,
-            "peak_admitted_bytes": peak, "summary": summ,
+            "capacity_closed_loop": cap, "arrival_rate_per_s": rate, "hbm_budget_bytes": budget,
+            "peak_admitted_bytes": peak, "summary": summ, "stacks_raised": raised,
             "full_scale": None if not full_res else {
                 "status": full_res[0].status, "error": full_res[0].error,
                 "latency_s": full_res[0].latency, "n_vis": full_res[0].n_vis,
-                "device_bytes": full_res[0].device_bytes},
+                "n_kept": full_res[0].n_kept, "device_bytes": full_res[0].device_bytes},
             "fp32_vs_fp64_reduced_stream": cmp}
     print(json.dumps(line), flush=True)
 

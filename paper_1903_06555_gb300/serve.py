@@ -36,7 +36,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import PhiError, Plan
+from . import PHI_ERR_SUPPORT, PhiError, Plan
 
 __all__ = ["Request", "Result", "Server", "estimate_bytes"]
 
@@ -51,6 +51,7 @@ class Request:
     ops: tuple = ("degrid",)        # any of "degrid", "grid" (grid of the degrid output if both)
     arrival: float = 0.0            # seconds after the stream starts
     obs_key: str | None = None      # keep/reuse the plan under this key
+    raise_stacks: bool = False      # on PHI_ERR_SUPPORT retry with twice the stacks (<= 126)
 
 
 @dataclass
@@ -67,6 +68,8 @@ class Result:
     done: float = 0.0
     plan_reused: bool = False
     device_bytes: int = 0
+    n_kept: int = 0                 # visibilities inside the grid (w-corrected)
+    n_stacks: int = 0               # stacks used (after any raising)
 
     @property
     def latency(self):
@@ -228,8 +231,21 @@ class Server:
                     res.plan_reused = True
                 else:
                     uvw = torch.from_numpy(np.ascontiguousarray(req.uvw, np.float64)).pin_memory()
-                    plan = Plan(uvw.to(self.device, non_blocking=True), stream=stream, **req.desc)
-                res.device_bytes = plan.info()["device_bytes"]
+                    uvw_d = uvw.to(self.device, non_blocking=True)
+                    desc = dict(req.desc)
+                    while True:
+                        try:
+                            plan = Plan(uvw_d, stream=stream, **desc)
+                            break
+                        except PhiError as e:
+                            k = int(desc.get("n_stacks", 1))
+                            if e.status != PHI_ERR_SUPPORT or not req.raise_stacks or k >= 126:
+                                raise
+                            desc["n_stacks"] = min(126, 2 * k)
+                info = plan.info()
+                res.device_bytes = info["device_bytes"]
+                res.n_kept = info["n_kept"]
+                res.n_stacks = info["n_stacks"]
                 y = None
                 if "degrid" in req.ops:
                     x = torch.from_numpy(np.ascontiguousarray(req.image)).pin_memory()
@@ -281,8 +297,10 @@ def summarize(results, t_first=None):
     lat = np.array([r.latency for r in ok])
     t0 = min(r.arrival for r in results) if t_first is None else t_first
     t1 = max(r.done for r in ok)
-    nvis = sum(r.n_vis for r in ok)
-    return {"ok": len(ok), "errors": len(results) - len(ok), "vis": nvis,
+    nvis = sum(r.n_kept for r in ok)
+    errs = collections.Counter(r.error.split(":")[-1].strip() for r in results if r.status != "ok")
+    return {"ok": len(ok), "errors": len(results) - len(ok), "error_kinds": dict(errs), "vis": nvis,
+            "vis_submitted": sum(r.n_vis for r in ok),
             "makespan_s": t1 - t0, "vis_per_s": nvis / (t1 - t0),
             "latency_p50_s": float(np.percentile(lat, 50)),
             "latency_p99_s": float(np.percentile(lat, 99)),
