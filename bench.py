@@ -83,12 +83,29 @@ def barrier(ws):
 
 
 def max_over_ranks(v, ws):
+    """The largest value over all ranks (the slowest rank's time)."""
     if ws == 1:
         return v
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(ms_step_local, n_units_local, ws):
+    """Whole-job throughput of N independent replicas: the units all ranks
+    processed over the slowest rank's step time.  Returns (value, ms)."""
+    ms = max_over_ranks(ms_step_local, ws)
+    if ws > 1:
+        import torch.distributed as dist
+        dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+        t = torch.tensor([float(n_units_local)], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        n_total = float(t.item())
+    else:
+        n_total = float(n_units_local)
+    return n_total / (ms / 1e3), ms
 
 
 class ClockSampler:
@@ -327,8 +344,7 @@ def run_ours(args, ws, rank, local):
     stages = plan.timings(reset=True)
     bad, taps, tap_nodes = plan.stats_full(reset=True)
     ms_step = sum(times) / len(times)
-    ms_step_max = max_over_ranks(ms_step, ws)
-    value = ws * n_kept / (ms_step_max / 1e3)
+    value, ms_step_max = aggregate_value(ms_step, n_kept, ws)
     lat = sorted(times)
     p50 = statistics.median(lat)
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
