@@ -77,6 +77,15 @@ def lib():
             f.argtypes = [c_double_p, i64, c_double_p, c_double_p, i64, c_double_p,
                           c_double_p, c_double_p, c_int32_p, c_double_p, c_uint8_p,
                           c_double_p, c_int64_p, c_int64_p]
+        L.orc_table_kernel.restype = None
+        L.orc_table_kernel.argtypes = [c_double_p, c_double_p, i64, c_double_p, i64, i64, d, d,
+                                       c_double_p]
+        L.orc_degrid_table.restype = None
+        L.orc_degrid_table.argtypes = [c_double_p, i64, c_double_p, i64, i64, d, d, i64,
+                                       c_double_p, c_double_p, c_double_p, c_int32_p, c_double_p,
+                                       c_uint8_p, c_double_p]
+        L.orc_grid_table.restype = None
+        L.orc_grid_table.argtypes = L.orc_degrid_table.argtypes
         L.orc_kmeans.restype = ctypes.c_int
         L.orc_kmeans.argtypes = [c_double_p, i64, i32, i32, d, c_int32_p, c_double_p]
         _LIB = L
@@ -548,6 +557,108 @@ def grid(plan: OraclePlan, y, tol_rel=None, tol_abs=None, return_stats=False):
     grids, ev, bad = grid_to_stacks(plan, y, None, tol_rel, tol_abs)
     x = image_from_grids(plan, grids)
     return (x, ev, bad) if return_stats else x
+
+
+# ----------------------------------------------------------------------------
+# Pre-sampled 1-D w-planes (Sec. 5.1.1)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class KernelTable:
+    """[GC](i hr, j hw) for i < nr, j < nw: positive rho and w only (Sec.
+    5.1.1: the conjugate gives -w, radial symmetry gives negative u, v)."""
+    hr: float
+    hw: float
+    values: np.ndarray      # complex128 (nw, nr)
+
+    @property
+    def nr(self):
+        return self.values.shape[1]
+
+    @property
+    def nw(self):
+        return self.values.shape[0]
+
+
+def table_spacing(geo: Geometry, table_tol: float):
+    """Sample spacing for a bilinear interpolation error <= table_tol.  The
+    bilinear error is at most h^2/8 times the second derivative in each
+    direction (half the budget each); the integrand's rho- and w-dependence
+    (J0(2 pi rho r), e^{2 pi i w (1 - n(r))}) bounds those by (2 pi R)^2 and
+    (2 pi (1 - n(R)))^2 times 2 pi int g r dr, taken as 1."""
+    hr = math.sqrt(4.0 * table_tol) / (2.0 * math.pi * geo.R)
+    hw = math.sqrt(4.0 * table_tol) / (2.0 * math.pi * (1.0 - geo.n_win))
+    return hr, hw
+
+
+def table_extent(plan: OraclePlan):
+    """Largest tap radius and |dw| the plan can ask for: sqrt(2) J_max / 2
+    (plus a margin) and the largest |dw| of its kept visibilities."""
+    keep = ~plan.dropped
+    jmax = int(plan.jw[keep].max()) if keep.any() else int(plan.geo.J)
+    dmax = float(np.max(np.abs(plan.dw[keep]))) if keep.any() else 0.0
+    return math.sqrt(2.0) * jmax / 2.0 + 2.0, dmax
+
+
+def make_table(plan: OraclePlan, table_tol: float, tol_rel=None, tol_abs=None) -> KernelTable:
+    hr, hw = table_spacing(plan.geo, table_tol)
+    rmax, dmax = table_extent(plan)
+    nr = int(math.ceil(rmax / hr)) + 2
+    nw = int(math.ceil(dmax / hw)) + 2
+    rho = np.arange(nr) * hr
+    w = np.arange(nw) * hw
+    R, Wg = np.meshgrid(rho, w)
+    vals = wkernel(R.ravel(), Wg.ravel(), plan.geo, tol_rel, tol_abs).reshape(nw, nr)
+    return KernelTable(hr, hw, np.ascontiguousarray(vals))
+
+
+def table_kernel(table: KernelTable, rho, dw):
+    rho = np.ascontiguousarray(np.atleast_1d(np.asarray(rho, np.float64)))
+    dw = np.ascontiguousarray(np.broadcast_to(np.asarray(dw, np.float64), rho.shape))
+    out = np.zeros(2 * rho.size)
+    lib().orc_table_kernel(_p(rho), _p(dw), rho.size, table.values.view(np.float64).ctypes.data_as(
+        c_double_p), table.nr, table.nw, table.hr, table.hw, _p(out))
+    return out[0::2] + 1j * out[1::2]
+
+
+def degrid_table(plan: OraclePlan, x, table: KernelTable, subset=None):
+    """y = Phi x with every tap read from the table."""
+    geo = plan.geo
+    sel = np.arange(plan.flag.size) if subset is None else np.asarray(subset)
+    grids = stack_grids(plan, x, sorted(set(int(k) for k in plan.stack[sel])))
+    y = np.zeros(sel.size, np.complex128)
+    tab = table.values.view(np.float64).ctypes.data_as(c_double_p)
+    for k, g in grids.items():
+        pos = np.nonzero(plan.stack[sel] == k)[0]
+        sub = sel[pos]
+        u, v, d, j, wt, fl = _vis_args(plan, sub)
+        out = np.zeros(2 * sub.size)
+        lib().orc_degrid_table(g.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, tab,
+                               table.nr, table.nw, table.hr, table.hw, sub.size, _p(u), _p(v),
+                               _p(d), _p(j, c_int32_p), _p(wt), _p(fl, c_uint8_p), _p(out))
+        y[pos] = out[0::2] + 1j * out[1::2]
+    return y
+
+
+def grid_table(plan: OraclePlan, y, table: KernelTable):
+    """x = Re(Phi^H y) with every tap read from the table."""
+    geo = plan.geo
+    y = np.asarray(y, np.complex128)
+    grids = {}
+    tab = table.values.view(np.float64).ctypes.data_as(c_double_p)
+    for k in range(plan.n_stacks):
+        idx = np.nonzero(plan.stack == k)[0]
+        if idx.size == 0:
+            continue
+        g = np.zeros((geo.Npad, geo.Npad), np.complex128)
+        u, v, d, j, wt, fl = _vis_args(plan, idx)
+        yk = np.ascontiguousarray(y[idx])
+        lib().orc_grid_table(g.view(np.float64).ctypes.data_as(c_double_p), geo.Npad, tab,
+                             table.nr, table.nw, table.hr, table.hw, idx.size, _p(u), _p(v),
+                             _p(d), _p(j, c_int32_p), _p(wt), _p(fl, c_uint8_p),
+                             yk.view(np.float64).ctypes.data_as(c_double_p))
+        grids[k] = g
+    return image_from_grids(plan, grids)
 
 
 def rel_l2(a, b):

@@ -381,3 +381,47 @@ def test_visibilities_outside_grid_are_dropped():
     assert list(plan.jw[:2]) == [0, 0]
     y = O.degrid(plan, np.ones((128, 128)))
     assert y[0] == 0 and y[1] == 0 and y[2] != 0
+
+
+# ---------------------------------------------------------------- pre-sampled w-planes
+
+@pytest.fixture(scope="module")
+def table_case():
+    geo = tiny_geo(tol_rel=1e-12, tol_abs=1e-12)
+    uvw = W.uvw_disk(60, 60.0, 40.0, 41)
+    plan = O.make_plan(uvw, geo, 2, True)
+    return geo, uvw, plan, O.make_table(plan, 1e-3)
+
+
+def test_table_reproduces_samples_and_meets_its_tolerance(table_case):
+    """Sec. 5.1.1: bilinear interpolation between 1-D w-planes.  At sample
+    points the table returns the quadrature value; in between, the error
+    stays inside the tolerance the spacing was derived from; negative w is
+    the conjugate (Sec. 5.1.1 / Sec. 3.3)."""
+    geo, _, plan, tab = table_case
+    i = np.array([0, 5, 17, tab.nr - 3])
+    j = np.array([0, 2, tab.nw // 2, tab.nw - 2])
+    k = O.table_kernel(tab, i * tab.hr, j * tab.hw)
+    assert np.allclose(k, tab.values[j, i], atol=1e-15)
+    rng = np.random.default_rng(2)
+    rmax, dmax = O.table_extent(plan)
+    rho = rng.uniform(0, rmax - 2, 300)
+    dw = rng.uniform(-dmax, dmax, 300)
+    err = np.abs(O.table_kernel(tab, rho, dw) - O.wkernel(rho, dw, geo))
+    assert err.max() <= 1e-3
+    assert np.allclose(O.table_kernel(tab, rho, -dw), np.conj(O.table_kernel(tab, rho, dw)))
+
+
+def test_table_operator_close_to_direct_operator(table_case):
+    """The tabulated operator differs from the quadrature operator by the
+    interpolation error only; its adjoint pairs exactly."""
+    geo, uvw, plan, tab = table_case
+    x = W.point_sources(128, 10, 41)
+    yq = O.degrid(plan, x)
+    yt = O.degrid_table(plan, x, tab)
+    assert O.rel_l2(yt, yq) < 2e-3
+    xr = W.random_image(128, 4)
+    yr = W.random_vis(len(uvw), 4)
+    lhs = np.real(np.vdot(yr, O.degrid_table(plan, xr, tab)))
+    rhs = float(np.sum(xr * O.grid_table(plan, yr, tab)))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
