@@ -58,6 +58,10 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cycles-per-panel", type=float, default=0.0,
                     help="a-priori quadrature panel width in integrand cycles (0: library default)")
+    ap.add_argument("--kernel-mode", default="quadrature", choices=["quadrature", "table"],
+                    help="quadrature: every tap integrated (the hot path); table: pre-sampled "
+                         "1-D w-planes with bilinear interpolation (Sec. 5.1.1)")
+    ap.add_argument("--table-tol", type=float, default=1e-4)
     ap.add_argument("--max-vis", type=int, default=0,
                     help="use only the first N visibilities (small profiling case)")
     return ap.parse_args()
@@ -294,7 +298,8 @@ def run_ours(args, ws, rank, local):
     desc = dict(image_n=wl.image_n, fov_rad=math.radians(wl.fov_deg), oversample=wl.oversample,
                 support=wl.support, n_stacks=wl.n_stacks, conj_fold=int(wl.conj_fold),
                 precision="f32", support_rule=args.support_rule,
-                cycles_per_panel=args.cycles_per_panel)
+                cycles_per_panel=args.cycles_per_panel, kernel_mode=args.kernel_mode,
+                table_tol=args.table_tol)
     stream = torch.cuda.current_stream()
     uvw = torch.from_numpy(uvw_np).to(dev)
     torch.cuda.synchronize()
@@ -349,6 +354,20 @@ def run_ours(args, ws, rank, local):
     p50 = statistics.median(lat)
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
 
+    table_info = None
+    if args.kernel_mode == "table":
+        qdesc = dict(desc, kernel_mode="quadrature")
+        qplan = phi.Plan(uvw, **qdesc)
+        yq = qplan.degrid(x)
+        yt = plan.degrid(x)
+        qplan.close()
+        table_info = {"table_tol": args.table_tol, "n_rho": info["table_n_rho"],
+                      "n_w": info["table_n_w"], "h_rho": info["table_h_rho"],
+                      "h_w": info["table_h_w"],
+                      "bytes": 16 * info["table_n_rho"] * (info["table_n_w"] - 1),
+                      "rel_l2_vs_quadrature_path": float(torch.linalg.vector_norm(yt - yq) /
+                                                         torch.linalg.vector_norm(yq))}
+
     # roofline: the dominant kernel (fused quadrature + degrid or + grid)
     counts = load_oracle_counts()
     evals_per_vis = counts["evals_per_vis_mean"]
@@ -390,6 +409,8 @@ def run_ours(args, ws, rank, local):
                                   f"{sm_mhz:.0f} MHz (recipe unit counts, max clock)",
                      "work_note": f"{FLOPS_PER_TAP_NODE:.0f} flops per tap-node x oracle tap-nodes "
                                   f"per visibility at tol 1e-6"},
+        "kernel_mode": args.kernel_mode,
+        "table": table_info,
         "e2e": e2e,
         "gpu_launches": int(4 * sum(1 for c in info["counts"] if c > 0) * args.steps),
         "clocks": clocks,

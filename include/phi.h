@@ -79,6 +79,11 @@ enum phi_precision {
   PHI_F64 = 1   /* everything in FP64                                        */
 };
 
+enum phi_kernel_mode {
+  PHI_KERNEL_QUADRATURE = 0,  /* every tap by adaptive quadrature (Sec. 3.1)         */
+  PHI_KERNEL_TABLE = 1        /* pre-sampled 1-D w-planes, bilinear (Sec. 5.1.1)       */
+};
+
 enum phi_support_rule {
   PHI_SUPPORT_STACK = 0,  /* J_w per stack from its largest |w - wbar_k|     */
   PHI_SUPPORT_VIS = 1     /* J_w per visibility from its own |w - wbar_k|    */
@@ -96,6 +101,8 @@ typedef struct {
   int32_t support_rule;     /* enum phi_support_rule                         */
   int32_t max_refine;       /* panel-count doublings allowed per tap chunk   */
   int32_t tile;             /* uv tile side used to sort visibilities (32)   */
+  int32_t kernel_mode;      /* enum phi_kernel_mode                          */
+  int32_t reserved0;        /* must be 0                                     */
   double oversample;        /* os; Npad = os * N must be an even integer     */
   double fov_rad;           /* full field of view in direction cosine        */
   double kmeans_tol;        /* Algorithm 1 convergence (default 1e-3)        */
@@ -104,6 +111,10 @@ typedef struct {
   double quad_abs_tol;      /* default 1e-6 (Sec. 4)                         */
   double kb_beta;           /* 0: pi sqrt((J/os)^2 (os - 1/2)^2 - 0.8)        */
   double cycles_per_panel;  /* a-priori panel width in integrand cycles (0: auto) */
+  double table_tol;         /* PHI_KERNEL_TABLE: bilinear interpolation error bound
+                               (default 1e-4); sample spacing
+                               h_rho = sqrt(4 tol) / (2 pi R),
+                               h_w = sqrt(4 tol) / (2 pi (1 - n(R / du)))  */
 } phi_plan_desc;
 
 /* Plan summary filled by phi_plan_info. */
@@ -114,6 +125,12 @@ typedef struct {
   int64_t device_bytes;     /* device memory held by the plan                */
   int32_t image_n, npad, n_stacks, kmeans_sweeps, max_jw, precision;
   double du, dl, beta, window_radius, support_coeff;
+  int32_t kernel_mode;      /* enum phi_kernel_mode                          */
+  int32_t reserved0;
+  int64_t table_n_rho;      /* PHI_KERNEL_TABLE: samples in rho (0 otherwise) */
+  int64_t table_n_w;        /* samples in |w|                                */
+  double table_h_rho;       /* spacing in grid pixels                        */
+  double table_h_w;         /* spacing in wavelengths                        */
 } phi_plan_summary;
 
 /* Fill *desc with the defaults (image size, FOV and stack count are 0 and
@@ -124,11 +141,18 @@ int phi_plan_desc_default(phi_plan_desc* desc);
  * Build a plan (Sec. 3.2-3.3 and the per-visibility part of Eq. GC_k):
  * fold (conj_fold), Algorithm 1 on w, per-stack centres wbar_k, drop test,
  * support J_w, split u/du into integer base and fraction, sort by
- * (stack, uv tile), per-pixel image factors, cuFFT plan.
+ * (stack, uv tile), per-pixel image factors, cuFFT plan.  With
+ * PHI_KERNEL_TABLE also the pre-sampled w-planes of Sec. 5.1.1:
+ * [GC](i h_rho, j h_w) for 0 <= rho <= sqrt(2) max J_w / 2 + 2 and
+ * 0 <= w <= max |w - wbar_k| (positive only: -w is the conjugate), computed
+ * by the same adaptive quadrature, stored in pairs of adjacent w-planes;
+ * degrid and grid then interpolate every tap bilinearly instead of
+ * integrating it.
  *   uvw_dev:     n_vis x 3 float64 (u, v, w in wavelengths), row-major, device.
  *   weights_dev: n_vis float64 weights W_i (Eq. matrix_equation), or NULL for 1.
  *   n_vis:       >= 0.
- * The input buffers are only read during the call.  Returns PHI_ERR_ARG,
+ * The input buffers are only read during the call; a non-finite u, v or w
+ * is PHI_ERR_ARG.  Returns PHI_ERR_ARG,
  * PHI_ERR_HORIZON, PHI_ERR_SUPPORT, PHI_ERR_OOM or PHI_ERR_CUDA on failure
  * (then *out is NULL).  Synchronises `stream`.
  */

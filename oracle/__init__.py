@@ -396,6 +396,8 @@ def make_plan(uvw, geo: Geometry, n_stacks=1, conj_fold=False, weights=None,
     visibility to its nearest given centre (lowest index on ties), and the
     centres are kept; with `stack_jw` the per-stack supports are given."""
     uvw = np.asarray(uvw, dtype=np.float64)
+    if not np.all(np.isfinite(uvw)):
+        raise ValueError("non-finite baseline coordinates")
     if conj_fold:
         uvw, flag = fold(uvw)
     else:

@@ -31,6 +31,7 @@ PHI_OK, PHI_ERR_ARG, PHI_ERR_OOM, PHI_ERR_CUDA, PHI_ERR_HORIZON, PHI_ERR_SUPPORT
     PHI_ERR_TIMEOUT, PHI_ERR_STATE = range(8)
 PHI_F32, PHI_F64 = 0, 1
 PHI_SUPPORT_STACK, PHI_SUPPORT_VIS = 0, 1
+PHI_KERNEL_QUADRATURE, PHI_KERNEL_TABLE = 0, 1
 STAGES = ("prep", "fft", "degrid", "grid", "finish", "clear")
 NUM_STAGES = len(STAGES)
 
@@ -48,6 +49,8 @@ class PlanDesc(ctypes.Structure):
         ("support_rule", ctypes.c_int32),
         ("max_refine", ctypes.c_int32),
         ("tile", ctypes.c_int32),
+        ("kernel_mode", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
         ("oversample", ctypes.c_double),
         ("fov_rad", ctypes.c_double),
         ("kmeans_tol", ctypes.c_double),
@@ -56,6 +59,7 @@ class PlanDesc(ctypes.Structure):
         ("quad_abs_tol", ctypes.c_double),
         ("kb_beta", ctypes.c_double),
         ("cycles_per_panel", ctypes.c_double),
+        ("table_tol", ctypes.c_double),
     ]
 
 
@@ -77,6 +81,12 @@ class PlanSummary(ctypes.Structure):
         ("beta", ctypes.c_double),
         ("window_radius", ctypes.c_double),
         ("support_coeff", ctypes.c_double),
+        ("kernel_mode", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("table_n_rho", ctypes.c_int64),
+        ("table_n_w", ctypes.c_int64),
+        ("table_h_rho", ctypes.c_double),
+        ("table_h_w", ctypes.c_double),
     ]
 
 
@@ -165,6 +175,8 @@ def default_desc(**kw) -> PlanDesc:
             v = {"f32": PHI_F32, "f64": PHI_F64}[v]
         if k == "support_rule" and isinstance(v, str):
             v = {"stack": PHI_SUPPORT_STACK, "vis": PHI_SUPPORT_VIS}[v]
+        if k == "kernel_mode" and isinstance(v, str):
+            v = {"quadrature": PHI_KERNEL_QUADRATURE, "table": PHI_KERNEL_TABLE}[v]
         if not hasattr(d, k):
             raise TypeError(f"unknown descriptor field {k}")
         setattr(d, k, type(getattr(d, k))(v))

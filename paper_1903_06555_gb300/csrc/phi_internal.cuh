@@ -131,6 +131,12 @@ struct Plan {
   bool fft_ok = false;
   int64_t device_bytes = 0;
   int num_sms = 0;
+  // pre-sampled w-planes (PHI_KERNEL_TABLE): (nw - 1) x nr pairs
+  // {K(j h_w, i h_rho), K((j + 1) h_w, i h_rho)} of precision T
+  void* table = nullptr;
+  int64_t table_nr = 0, table_nw = 0;
+  double table_hr = 0, table_hw = 0;
+  std::vector<double> stack_maxabs;   // largest |w - wbar_k| of each stack's kept visibilities
 
   QuadParams quad() const {
     QuadParams q;
@@ -160,6 +166,14 @@ struct Plan {
     }                                            \
   } while (0)
 
+// Kernel-side view of the pre-sampled w-planes.
+template <typename T>
+struct TableView {
+  const void* pairs;   // C2<T> [(nw - 1) * nr]
+  int64_t nr, nw;
+  T inv_hr, inv_hw;
+};
+
 // Stage timing (no-ops unless enabled): returns the start-event index or -1.
 long timer_begin(Plan& p, cudaStream_t s);
 void timer_end(Plan& p, long idx, int stage, cudaStream_t s);
@@ -167,6 +181,7 @@ void timer_end(Plan& p, long idx, int stage, cudaStream_t s);
 // Launchers implemented in phi_ops.cu.
 int launch_node_tables(Plan& p, cudaStream_t s);
 int launch_pixel_tables(Plan& p, cudaStream_t s);
+int build_kernel_table(Plan& p, cudaStream_t s);
 
 }  // namespace phi
 

@@ -457,6 +457,146 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pre-sampled 1-D w-planes (Sec. 5.1.1)
+// ---------------------------------------------------------------------------
+
+// Two adjacent w-planes at one radius: {K(j, i), K(j + 1, i)}.
+template <typename C> struct __align__(2 * sizeof(C)) KPair { C a, b; };
+
+// Sample K(i h_rho, j h_w) for all i < nr, j < nw: one warp per w-plane,
+// lanes over radii, 32 radii per chunk sharing one node set (the same
+// quadrature routine as the degridder).
+template <typename T, typename C>
+__global__ void __launch_bounds__(256) table_sample_kernel(C* __restrict__ raw, int64_t nr,
+                                                           int64_t nw, double hr, double hw,
+                                                           QuadParams q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
+  const int64_t wpb = blockDim.x >> 5;
+  unsigned long long nodes = 0;
+  for (int64_t j = blockIdx.x * wpb + warp; j < nw; j += (int64_t)gridDim.x * wpb) {
+    const double w = static_cast<double>(j) * hw;
+    int built = 0;
+    for (int64_t i0 = 0; i0 < nr; i0 += 32) {
+      const int64_t i = i0 + lane;
+      const bool active = i < nr;
+      const T rho = static_cast<T>(static_cast<double>(active ? i : i0) * hr);
+      const int64_t ilast = min(i0 + 31, nr - 1);
+      const int npan = initial_panels(q, static_cast<float>(ilast * hr), static_cast<float>(w));
+      bool ok = true;
+      const C K = eval_chunk<T, C>(sh, q, rho, active, w, npan, built, ok, lane, nodes);
+      if (active) raw[j * nr + i] = K;
+    }
+  }
+}
+
+template <typename C>
+__global__ void table_pair_kernel(const C* __restrict__ raw, int64_t nr, int64_t nw,
+                                  KPair<C>* __restrict__ pairs) {
+  const int64_t total = (nw - 1) * nr;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    KPair<C> v;
+    v.a = raw[k];
+    v.b = raw[k + nr];
+    pairs[k] = v;
+  }
+}
+
+// Degrid / grid with every tap interpolated bilinearly in (rho, |dw|) from
+// the pre-sampled w-planes, conjugated for dw < 0.  One warp per visibility
+// (its two w-planes stay in L1 while its taps are read), taps in raster order.
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restrict__ recs,
+                                                        const uint32_t* __restrict__ perm,
+                                                        int64_t n, const C* __restrict__ grid_in,
+                                                        C* grid_out, const C* __restrict__ vis_in,
+                                                        C* __restrict__ vis_out, TableView<T> tv,
+                                                        int npad_i, unsigned long long* head,
+                                                        unsigned long long* stats) {
+  const int lane = threadIdx.x & 31;
+  const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
+  const int64_t npad = npad_i;
+  unsigned long long my_taps = 0;
+  while (true) {
+    unsigned long long i = 0;
+    if (lane == 0) i = atomicAdd(head, 1ULL);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= static_cast<unsigned long long>(n)) break;
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw;
+    const int half = Jw / 2;
+    const T fu = r.fu, fv = r.fv;
+    const T aw = static_cast<T>(fabs(r.dw)) * tv.inv_hw;
+    // the comparison also sends a NaN to the last row instead of an
+    // undefined conversion
+    const int64_t jrow = aw < static_cast<T>(tv.nw - 2) ? static_cast<int64_t>(aw) : tv.nw - 2;
+    const T fw = aw - static_cast<T>(jrow);
+    const bool neg = r.dw < 0.0;
+    const KPair<C>* row = pairs + jrow * tv.nr;
+    const uint32_t pm = perm[i];
+    C yv = cmake<C>(0.0, 0.0);
+    if (kGrid) {
+      C v = vis_in[pm & 0x7fffffffu];
+      if (pm >> 31) v.y = -v.y;
+      yv.x = v.x * static_cast<T>(r.weight);
+      yv.y = v.y * static_cast<T>(r.weight);
+    }
+    C accv = cmake<C>(0.0, 0.0);
+    const int ntap = Jw * Jw;
+    for (int t0 = 0; t0 < ntap; t0 += 32) {
+      const int t = t0 + lane;
+      if (t < ntap) {
+        const int a = t % Jw, b = t / Jw;
+        const int ou = a - half + 1, ov = b - half + 1;
+        const T du_ = fu - static_cast<T>(ou), dv_ = fv - static_cast<T>(ov);
+        const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
+        const int64_t ir = sr < static_cast<T>(tv.nr - 2) ? static_cast<int64_t>(sr) : tv.nr - 2;
+        const T fr = sr - static_cast<T>(ir);
+        const KPair<C> p0 = row[ir], p1 = row[ir + 1];
+        const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
+        const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
+        C K;
+        K.x = fma(fw, hi_x - lo_x, lo_x);
+        K.y = fma(fw, hi_y - lo_y, lo_y);
+        if (neg) K.y = -K.y;
+        ++my_taps;
+        const int64_t gi = pmod64(r.bv + ov, npad) * npad + pmod64(r.bu + ou, npad);
+        if (kGrid) {
+          C add;
+          add.x = K.x * yv.x + K.y * yv.y;
+          add.y = K.x * yv.y - K.y * yv.x;
+          atomic_add_c(grid_out + gi, add);
+        } else {
+          const C g = grid_in[gi];
+          accv.x += K.x * g.x - K.y * g.y;
+          accv.y += K.x * g.y + K.y * g.x;
+        }
+      }
+    }
+    if (!kGrid) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
+        accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
+      }
+      if (lane == 0) {
+        C out;
+        out.x = accv.x * static_cast<T>(r.weight);
+        out.y = accv.y * static_cast<T>(r.weight);
+        if (pm >> 31) out.y = -out.y;
+        vis_out[pm & 0x7fffffffu] = out;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
+  if (lane == 0 && my_taps) atomicAdd(stats + 1, my_taps);
+}
+
 // phi_wkernel: one warp per point, lane 0 carries the tap.
 template <typename T, typename C>
 __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__ rho_in,
@@ -503,6 +643,42 @@ int blocks_for_vis(const Plan& p, size_t smem) {
 }
 
 template <typename T, typename C>
+int build_table_t(Plan& p, cudaStream_t s) {
+  const int64_t nr = p.table_nr, nw = p.table_nw;
+  C* raw = nullptr;
+  PHI_CUDA_TRY(cudaMalloc(&raw, sizeof(C) * nr * nw));
+  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
+  const int64_t want = (nw + 7) / 8;
+  const int blocks = static_cast<int>(want < 65535 ? want : 65535);
+  table_sample_kernel<T, C><<<blocks, kVisThreads, smem, s>>>(raw, nr, nw, p.table_hr, p.table_hw,
+                                                              p.quad());
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) {
+    table_pair_kernel<C><<<p.num_sms * 8, 256, 0, s>>>(raw, nr, nw,
+                                                       static_cast<KPair<C>*>(p.table));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(raw);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return PHI_ERR_CUDA;
+  }
+  return PHI_OK;
+}
+
+template <typename T, typename C>
+TableView<T> table_view(const Plan& p) {
+  TableView<T> v;
+  v.pairs = p.table;
+  v.nr = p.table_nr;
+  v.nw = p.table_nw;
+  v.inv_hr = static_cast<T>(1.0 / p.table_hr);
+  v.inv_hw = static_cast<T>(1.0 / p.table_hw);
+  return v;
+}
+
+template <typename T, typename C>
 int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
   const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
   long ev = timer_begin(p, s);
@@ -533,9 +709,14 @@ int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
     if (fr != CUFFT_SUCCESS) return PHI_ERR_CUDA;
     timer_end(p, ev, PHI_STAGE_FFT, s);
     ev = timer_begin(p, s);
-    vis_kernel<T, C, false><<<vis_blocks, kVisThreads, smem, s>>>(
-        static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y, q,
-        p.counters + k, p.counters + p.K);
+    if (p.d.kernel_mode == PHI_KERNEL_TABLE)
+      vis_table_kernel<T, C, false><<<p.num_sms * 8, kVisThreads, 0, s>>>(
+          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y,
+          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K);
+    else
+      vis_kernel<T, C, false><<<vis_blocks, kVisThreads, smem, s>>>(
+          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y,
+          q, p.counters + k, p.counters + p.K);
     PHI_CUDA_TRY(cudaGetLastError());
     timer_end(p, ev, PHI_STAGE_DEGRID, s);
   }
@@ -558,9 +739,14 @@ int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
     PHI_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * (size_t)p.npad * p.npad, s));
     timer_end(p, ev, PHI_STAGE_CLEAR, s);
     ev = timer_begin(p, s);
-    vis_kernel<T, C, true><<<vis_blocks, kVisThreads, smem, s>>>(
-        static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr, q,
-        p.counters + k, p.counters + p.K);
+    if (p.d.kernel_mode == PHI_KERNEL_TABLE)
+      vis_table_kernel<T, C, true><<<p.num_sms * 8, kVisThreads, 0, s>>>(
+          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr,
+          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K);
+    else
+      vis_kernel<T, C, true><<<vis_blocks, kVisThreads, smem, s>>>(
+          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr,
+          q, p.counters + k, p.counters + p.K);
     PHI_CUDA_TRY(cudaGetLastError());
     timer_end(p, ev, PHI_STAGE_GRID, s);
     ev = timer_begin(p, s);
@@ -609,6 +795,11 @@ int run_wkernel(Plan& p, const double* rho, const double* dw, int64_t n, C* out,
 
 }  // namespace
 
+int build_kernel_table(Plan& p, cudaStream_t s) {
+  if (p.d.precision == PHI_F64) return build_table_t<double, double2>(p, s);
+  return build_table_t<float, float2>(p, s);
+}
+
 long timer_begin(Plan& p, cudaStream_t s) {
   if (!p.timing) return -1;
   size_t idx = 2 * p.ev_pending.size();
@@ -641,6 +832,10 @@ int set_kernel_smem_limits() {
   PHI_CUDA_TRY(cudaFuncSetAttribute(vis_kernel<double, double2, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
   PHI_CUDA_TRY(cudaFuncSetAttribute(wkernel_kernel<double, double2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(table_sample_kernel<float, float2>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(table_sample_kernel<double, double2>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
   return PHI_OK;
 }

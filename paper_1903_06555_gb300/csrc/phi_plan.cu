@@ -24,14 +24,21 @@ namespace {
 constexpr int kPlanThreads = 256;
 
 // Fold and extract w.  flag = 1 when the visibility was reflected.
+// Non-finite baselines are counted (the plan then refuses them).
 __global__ void fold_kernel(const double* __restrict__ uvw, int64_t M, int fold,
                             double* __restrict__ w_out, uint8_t* __restrict__ flag,
-                            double* __restrict__ part_min, double* __restrict__ part_max) {
+                            double* __restrict__ part_min, double* __restrict__ part_max,
+                            unsigned long long* __restrict__ n_bad) {
   __shared__ double smin[kPlanThreads], smax[kPlanThreads];
   double lo = INFINITY, hi = -INFINITY;
+  unsigned long long bad = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
        i += (int64_t)gridDim.x * blockDim.x) {
     double w = uvw[3 * i + 2];
+    if (!isfinite(uvw[3 * i]) || !isfinite(uvw[3 * i + 1]) || !isfinite(w)) {
+      ++bad;
+      w = 0.0;
+    }
     uint8_t f = (fold && w < 0.0) ? 1 : 0;
     if (f) w = -w;
     w_out[i] = w;
@@ -53,6 +60,7 @@ __global__ void fold_kernel(const double* __restrict__ uvw, int64_t M, int fold,
     part_min[blockIdx.x] = smin[0];
     part_max[blockIdx.x] = smax[0];
   }
+  if (bad) atomicAdd(n_bad, bad);
 }
 
 // One sweep of Algorithm 1: nearest centre by (wbar_q - w_p)^2 (strict <, so
@@ -252,6 +260,7 @@ void free_plan(Plan* p) {
   cudaFree(p->tap_off);
   cudaFree(p->grid);
   cudaFree(p->counters);
+  cudaFree(p->table);
 }
 
 template <typename X>
@@ -290,6 +299,10 @@ int validate(const phi_plan_desc& d, int64_t M) {
   if (d.max_refine < 0 || d.max_refine > 8) return PHI_ERR_ARG;
   if (d.tile < 0 || d.tile > 4096) return PHI_ERR_ARG;
   if (d.kb_beta < 0.0 || d.cycles_per_panel < 0.0) return PHI_ERR_ARG;
+  if (d.kernel_mode != PHI_KERNEL_QUADRATURE && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
+  if (d.reserved0 != 0) return PHI_ERR_ARG;
+  if (d.kernel_mode == PHI_KERNEL_TABLE && !(d.table_tol > 0.0 && d.table_tol < 1.0))
+    return PHI_ERR_ARG;
   return PHI_OK;
 }
 
@@ -363,6 +376,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   p.wbar.assign(K, 0.0);
   p.stack_off.assign(K + 1, 0);
   p.stack_jw.assign(K, 0);
+  p.stack_maxabs.assign(K, 0.0);
   PHI_CUDA_TRY(owned_alloc(p, &p.counters, static_cast<size_t>(K) + 4));
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * (K + 4), s));
 
@@ -386,13 +400,18 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   // --- fold and w range
   double wmin = 0.0, wmax = 0.0;
   if (M > 0) {
+    unsigned long long* n_bad = p.counters + K + 2;   // free until the operator runs
     fold_kernel<<<nblk, kPlanThreads, 0, s>>>(uvw, M, d.conj_fold ? 1 : 0, w_fold, flag, pmin,
-                                              pmax);
+                                              pmax, n_bad);
     PHI_CUDA_TRY(cudaGetLastError());
     std::vector<double> hmin(nblk), hmax(nblk);
+    unsigned long long hbad = 0;
     PHI_CUDA_TRY(cudaMemcpyAsync(hmin.data(), pmin, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
     PHI_CUDA_TRY(cudaMemcpyAsync(hmax.data(), pmax, sizeof(double) * nblk, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaMemcpyAsync(&hbad, n_bad, sizeof(hbad), cudaMemcpyDeviceToHost, s));
     PHI_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) return PHI_ERR_ARG;
+    PHI_CUDA_TRY(cudaMemsetAsync(n_bad, 0, sizeof(hbad), s));
     wmin = *std::min_element(hmin.begin(), hmin.end());
     wmax = *std::max_element(hmax.begin(), hmax.end());
   }
@@ -463,6 +482,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
     double maxabs;
     unsigned long long bits = hstat[q];
     std::memcpy(&maxabs, &bits, sizeof(double));
+    p.stack_maxabs[q] = hstat[K + q] ? maxabs : 0.0;
     p.stack_jw[q] = hstat[K + q] ? d.support + 2 * static_cast<int32_t>(std::ceil(maxabs * p.c_support)) : 0;
     if (fixed_jw && hstat[K + q]) p.stack_jw[q] = fixed_jw[q];
   }
@@ -522,6 +542,23 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
                            2 * tsize * static_cast<size_t>(p.npad) * p.npad));
   PHI_TRY(launch_node_tables(p, s));
   PHI_TRY(launch_pixel_tables(p, s));
+  if (d.kernel_mode == PHI_KERNEL_TABLE) {
+    // Sample spacing from the bilinear error bound (half the budget per
+    // direction): h^2/8 times the second derivative, bounded by (2 pi R)^2 in
+    // rho and (2 pi (1 - n_win))^2 in w.
+    p.table_hr = std::sqrt(4.0 * d.table_tol) / (2.0 * kPi * p.R);
+    p.table_hw = std::sqrt(4.0 * d.table_tol) / (2.0 * kPi * (1.0 - p.n_win));
+    double dmax = 0.0;
+    for (int q = 0; q < K; ++q) dmax = std::max(dmax, p.stack_maxabs[q]);
+    const double rmax = std::sqrt(2.0) * std::max(p.max_jw, d.support) / 2.0 + 2.0;
+    p.table_nr = static_cast<int64_t>(std::ceil(rmax / p.table_hr)) + 2;
+    p.table_nw = static_cast<int64_t>(std::ceil(dmax / p.table_hw)) + 2;
+    if (p.table_nr * p.table_nw > (int64_t(1) << 31)) return PHI_ERR_ARG;
+    const size_t pair = 2 * 2 * tsize;
+    PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.table),
+                             pair * (p.table_nw - 1) * p.table_nr));
+    PHI_TRY(build_kernel_table(p, s));
+  }
   if (cufftCreate(&p.fft) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
   p.fft_ok = true;
   size_t work = 0;
@@ -554,6 +591,8 @@ extern "C" int phi_plan_desc_default(phi_plan_desc* d) {
   d->quad_abs_tol = 1e-6;
   d->kb_beta = 0.0;
   d->cycles_per_panel = 0.0;
+  d->kernel_mode = PHI_KERNEL_QUADRATURE;
+  d->table_tol = 1e-4;
   return PHI_OK;
 }
 
@@ -632,6 +671,12 @@ extern "C" int phi_plan_info(phi_plan_t plan, phi_plan_summary* info, double* wb
     info->beta = p.beta;
     info->window_radius = p.R;
     info->support_coeff = p.c_support;
+    info->kernel_mode = p.d.kernel_mode;
+    info->reserved0 = 0;
+    info->table_n_rho = p.table_nr;
+    info->table_n_w = p.table_nw;
+    info->table_h_rho = p.table_hr;
+    info->table_h_w = p.table_hw;
   }
   for (int q = 0; q < p.K; ++q) {
     if (wbar) wbar[q] = p.wbar[q];

@@ -53,6 +53,10 @@ int main(void) {
   printf("phi_plan_summary %zu\n", sizeof(phi_plan_summary));
   O(phi_plan_desc, tile); O(phi_plan_desc, oversample); O(phi_plan_desc, cycles_per_panel);
   O(phi_plan_summary, image_n); O(phi_plan_summary, du); O(phi_plan_summary, support_coeff);
+  O(phi_plan_summary, kernel_mode); O(phi_plan_summary, table_n_rho); O(phi_plan_summary, table_h_w);
+  O(phi_plan_desc, kernel_mode); O(phi_plan_desc, table_tol);
+  printf("phi_wkernel_params %zu\n", sizeof(phi_wkernel_params));
+  O(phi_wkernel_params, cycles_per_panel); O(phi_wkernel_params, precision);
   return 0;
 }
 """
@@ -70,11 +74,13 @@ def test_struct_layout_matches_c():
     lay = _c_layout()
     assert int(lay["phi_plan_desc"]) == ctypes.sizeof(phi.PlanDesc)
     assert int(lay["phi_plan_summary"]) == ctypes.sizeof(phi.PlanSummary)
+    assert int(lay["phi_wkernel_params"]) == ctypes.sizeof(phi.WKernelParams)
+    classes = {"phi_plan_desc": phi.PlanDesc, "phi_plan_summary": phi.PlanSummary,
+               "phi_wkernel_params": phi.WKernelParams}
     for key, val in lay.items():
         if "." in key:
             t, f = key.split(".")
-            cls = phi.PlanDesc if t == "phi_plan_desc" else phi.PlanSummary
-            assert getattr(cls, f).offset == int(val), key
+            assert getattr(classes[t], f).offset == int(val), key
 
 
 def test_defaults_and_error_strings():
@@ -82,6 +88,7 @@ def test_defaults_and_error_strings():
     assert d.support == 4 and d.kmeans_max_iter == 100 and d.kmeans_tol == 1e-3
     assert d.quad_rel_tol == 1e-6 and d.quad_abs_tol == 1e-6 and d.alpha == 1.0
     assert d.max_support == 64 and d.precision == phi.PHI_F32
+    assert d.kernel_mode == phi.PHI_KERNEL_QUADRATURE and d.table_tol == 1e-4
     L = phi.lib()
     assert L.phi_error_string(0) == b"ok"
     for s in range(1, 8):
@@ -91,7 +98,8 @@ def test_defaults_and_error_strings():
 
 BAD = [dict(image_n=127), dict(image_n=0), dict(support=3), dict(n_stacks=0),
        dict(n_stacks=200), dict(precision=5), dict(oversample=1.25), dict(fov_rad=-1.0),
-       dict(max_support=2), dict(quad_rel_tol=0.0), dict(support_rule=3), dict(max_refine=-1)]
+       dict(max_support=2), dict(quad_rel_tol=0.0), dict(support_rule=3), dict(max_refine=-1),
+       dict(kernel_mode=2), dict(kernel_mode=1, table_tol=0.0), dict(reserved0=1)]
 
 
 @pytest.mark.parametrize("bad", BAD)
