@@ -109,9 +109,15 @@ __device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
   atomicAdd(&p->y, v.y);
 }
 
-__device__ __forceinline__ int64_t pmod64(int64_t a, int64_t n) {
-  int64_t r = a % n;
-  return r < 0 ? r + n : r;
+// Circular grid index q mod n in 32-bit arithmetic; the division only runs
+// for taps that actually cross the grid edge.  (64-bit integer division and
+// conversions execute on the FP64 unit, about 1/64 of the FP32 rate here.)
+__device__ __forceinline__ int wrap_index(int q, int n) {
+  if (static_cast<unsigned>(q) >= static_cast<unsigned>(n)) {
+    q %= n;
+    if (q < 0) q += n;
+  }
+  return q;
 }
 
 // 2-D transform of the radial Kaiser-Bessel kernel (support J = 2a, shape
@@ -376,7 +382,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
   const int warp = threadIdx.x >> 5;
   NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
-  const int64_t npad = q.npad;
+  const int npad = q.npad;
   while (true) {
     unsigned long long i = 0;
     if (lane == 0) i = atomicAdd(head, 1ULL);
@@ -416,7 +422,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
       if (active) {
         ++my_taps;
         if (!ok) ++my_bad;
-        const int64_t gi = pmod64(r.bv + ov, npad) * npad + pmod64(r.bu + ou, npad);
+        const int64_t gi = static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                           wrap_index(r.bu + ou, npad);
         if (kGrid) {
           C add;
           add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
@@ -460,6 +467,26 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
 // ---------------------------------------------------------------------------
 // Pre-sampled 1-D w-planes (Sec. 5.1.1)
 // ---------------------------------------------------------------------------
+
+// Table position of a scaled radius s >= 0: ir = floor(s) clamped to
+// last, fr = s - ir.  FP32 uses the 2^23 shift so no conversion instruction
+// is needed (an exact integer s may come out as ir = s - 1, fr = 1: the
+// same interpolated value).
+__device__ __forceinline__ void table_index(float s, int last, float last_f, int& ir, float& fr) {
+  const float big = 8388608.0f;                       // 2^23
+  const float t = (s - 0.5f) + big;                   // low bits: nearest integer to s - 1/2
+  ir = __float_as_int(t) - __float_as_int(big);
+  fr = s - (t - big);
+  if (!(s < last_f)) {                                // beyond the table (or NaN)
+    ir = last;
+    fr = s - last_f;
+  }
+}
+__device__ __forceinline__ void table_index(double s, int last, double last_f, int& ir,
+                                            double& fr) {
+  ir = s < last_f ? static_cast<int>(s) : last;
+  fr = s - static_cast<double>(ir);
+}
 
 // Two adjacent w-planes at one radius: {K(j, i), K(j + 1, i)}.
 template <typename C> struct __align__(2 * sizeof(C)) KPair { C a, b; };
@@ -519,7 +546,8 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
                                                         unsigned long long* stats) {
   const int lane = threadIdx.x & 31;
   const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
-  const int64_t npad = npad_i;
+  const int npad = npad_i;
+  const int nr = static_cast<int>(tv.nr), nw = static_cast<int>(tv.nw);
   unsigned long long my_taps = 0;
   while (true) {
     unsigned long long i = 0;
@@ -533,10 +561,10 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
     const T aw = static_cast<T>(fabs(r.dw)) * tv.inv_hw;
     // the comparison also sends a NaN to the last row instead of an
     // undefined conversion
-    const int64_t jrow = aw < static_cast<T>(tv.nw - 2) ? static_cast<int64_t>(aw) : tv.nw - 2;
+    const int jrow = aw < static_cast<T>(nw - 2) ? static_cast<int>(aw) : nw - 2;
     const T fw = aw - static_cast<T>(jrow);
     const bool neg = r.dw < 0.0;
-    const KPair<C>* row = pairs + jrow * tv.nr;
+    const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
     const uint32_t pm = perm[i];
     C yv = cmake<C>(0.0, 0.0);
     if (kGrid) {
@@ -547,15 +575,22 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
     }
     C accv = cmake<C>(0.0, 0.0);
     const int ntap = Jw * Jw;
+    // Tap t = b Jw + a, advanced by 32 per chunk without a division per tap;
+    // the offsets are also kept as floats so that no tap needs an int <-> float
+    // conversion (those run on the FP64 unit here).
+    int a = lane % Jw, b = lane / Jw;
+    const int step_b = 32 / Jw, step_a = 32 % Jw;
+    T du_ = fu - static_cast<T>(a - half + 1), dv_ = fv - static_cast<T>(b - half + 1);
+    const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
+    const T fJw = static_cast<T>(Jw), last_r = static_cast<T>(nr - 2);
     for (int t0 = 0; t0 < ntap; t0 += 32) {
       const int t = t0 + lane;
       if (t < ntap) {
-        const int a = t % Jw, b = t / Jw;
         const int ou = a - half + 1, ov = b - half + 1;
-        const T du_ = fu - static_cast<T>(ou), dv_ = fv - static_cast<T>(ov);
         const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
-        const int64_t ir = sr < static_cast<T>(tv.nr - 2) ? static_cast<int64_t>(sr) : tv.nr - 2;
-        const T fr = sr - static_cast<T>(ir);
+        int ir;
+        T fr;
+        table_index(sr, nr - 2, last_r, ir, fr);
         const KPair<C> p0 = row[ir], p1 = row[ir + 1];
         const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
         const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
@@ -564,7 +599,8 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
         K.y = fma(fw, hi_y - lo_y, lo_y);
         if (neg) K.y = -K.y;
         ++my_taps;
-        const int64_t gi = pmod64(r.bv + ov, npad) * npad + pmod64(r.bu + ou, npad);
+        const int64_t gi = static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                           wrap_index(r.bu + ou, npad);
         if (kGrid) {
           C add;
           add.x = K.x * yv.x + K.y * yv.y;
@@ -575,6 +611,16 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
           accv.x += K.x * g.x - K.y * g.y;
           accv.y += K.x * g.y + K.y * g.x;
         }
+      }
+      a += step_a;
+      b += step_b;
+      du_ -= fstep_a;
+      dv_ -= fstep_b;
+      if (a >= Jw) {
+        a -= Jw;
+        ++b;
+        du_ += fJw;
+        dv_ -= T(1);
       }
     }
     if (!kGrid) {
