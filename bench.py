@@ -48,8 +48,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mwa", choices=["mwa", "serve"],
-                    help="mwa: the headline operator benchmark; serve: the serving stream")
+    ap.add_argument("--workload", default="mwa", choices=["mwa", "serve", "plan"],
+                    help="mwa: the headline operator benchmark; serve: the serving stream; "
+                         "plan: Algorithm 1 and the fold at the paper's scale")
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-full-scale", type=int, default=1,
                     help="append the 126.6M-visibility request to the serving stream")
@@ -559,6 +560,62 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_plan_study(args):
+    """Plan building (fold, Algorithm 1, sort, tables) and kernel
+    construction (one degrid: every tap's kernel integrated once) with the
+    conjugate fold on and off, on the MWA-like snapshot (8 stacks) and at the
+    paper's scale (126.6M visibilities, |w| <= 600 after the fold, 1200
+    before, 50 stacks, 2048^2 image; Sec. 4)."""
+    import paper_1903_06555_gb300 as phi
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = []
+    n_times = -(-126_600_000 // 8128)
+    cases = [("mwa-2048-8stack", W.uvw_for(W.mwa_snapshot()), 2048, 8),
+             ("paper-scale-126.6M-50stack",
+              W.uvw_earth_rotation(128, 3000.0, 150e6, -26.7, -37.2, -n_times / 240,
+                                   n_times / 240, n_times, wmax=600.0, seed=5)[:126_600_000],
+              2048, 50)]
+    for name, uvw_np, n_img, k in cases:
+        uvw = torch.from_numpy(np.ascontiguousarray(uvw_np)).to(dev)
+        x = torch.from_numpy(W.point_sources(n_img, 200, 0)).to(dev, torch.float32)
+        for fold in (1, 0):
+            rec = {"case": name, "conj_fold": fold, "n_vis": int(uvw.shape[0]), "n_stacks": k}
+            try:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                plan = phi.Plan(uvw, image_n=n_img, fov_rad=math.radians(25.0), n_stacks=k,
+                                conj_fold=fold, max_support=256)
+                torch.cuda.synchronize()
+                rec["plan_ms"] = 1e3 * (time.perf_counter() - t0)
+                info = plan.info()
+                cnt = np.array(info["counts"], float)
+                jw = np.array(info["jw"], float)
+                rec.update(kmeans_sweeps=info["kmeans_sweeps"], n_kept=info["n_kept"],
+                           max_jw=info["max_jw"],
+                           mean_jw2=float((cnt * jw ** 2).sum() / max(cnt.sum(), 1)),
+                           w_span=float(max(info["wbar"]) - min(info["wbar"])))
+                plan.degrid(x)
+                plan.stats_full(reset=True)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                plan.degrid(x)
+                torch.cuda.synchronize()
+                rec["kernel_construction_s"] = time.perf_counter() - t0
+                bad, taps, nodes = plan.stats_full(reset=True)
+                rec.update(taps=taps, tap_nodes=nodes, unconverged=bad,
+                           kernels_per_s=info["n_kept"] / rec["kernel_construction_s"])
+                plan.close()
+            except phi.PhiError as e:
+                rec["error"] = str(e)
+            out.append(rec)
+            print(json.dumps(rec), flush=True)
+    line = {"metric": "plan build and kernel construction, conjugate fold on/off",
+            "paper_context": "Sec. 4: 126.6M visibilities, 50 stacks: k-means < 5 s in 6 "
+                             "iterations; kernel construction 15 min on 50 nodes (800 cores)",
+            "cases": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -567,6 +624,9 @@ def main():
     elif args.workload == "serve":
         if rank == 0:
             run_serve(args)
+    elif args.workload == "plan":
+        if rank == 0:
+            run_plan_study(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
