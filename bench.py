@@ -63,6 +63,9 @@ def parse():
                     help="quadrature: every tap integrated (the hot path); table: pre-sampled "
                          "1-D w-planes with bilinear interpolation (Sec. 5.1.1)")
     ap.add_argument("--table-tol", type=float, default=1e-4)
+    ap.add_argument("--tile", type=int, default=32, help="uv tile side of the visibility sort")
+    ap.add_argument("--grid-staging", type=int, default=0,
+                    help="table path: 0 one warp per visibility, 1 uv tiles staged in shared memory")
     ap.add_argument("--max-vis", type=int, default=0,
                     help="use only the first N visibilities (small profiling case)")
     return ap.parse_args()
@@ -299,7 +302,7 @@ def run_ours(args, ws, rank, local):
                 support=wl.support, n_stacks=wl.n_stacks, conj_fold=int(wl.conj_fold),
                 precision="f32", support_rule=args.support_rule,
                 cycles_per_panel=args.cycles_per_panel, kernel_mode=args.kernel_mode,
-                table_tol=args.table_tol)
+                table_tol=args.table_tol, tile=args.tile, grid_staging=args.grid_staging)
     stream = torch.cuda.current_stream()
     uvw = torch.from_numpy(uvw_np).to(dev)
     torch.cuda.synchronize()
@@ -623,6 +626,20 @@ def run_plan_study(args):
                 rec.update(taps=taps, tap_nodes=nodes, unconverged=bad,
                            kernels_per_s=info["n_kept"] / rec["kernel_construction_s"])
                 plan.close()
+                if fold:
+                    for staged in (0, 1):
+                        tp = phi.Plan(uvw, image_n=n_img, fov_rad=math.radians(25.0), n_stacks=k,
+                                      conj_fold=fold, max_support=256, kernel_mode="table",
+                                      grid_staging=staged)
+                        y = tp.degrid(x)
+                        tp.grid(y)
+                        torch.cuda.synchronize()
+                        t0 = time.perf_counter()
+                        y = tp.degrid(x)
+                        tp.grid(y)
+                        torch.cuda.synchronize()
+                        rec[f"table_degrid_grid_s_staging{staged}"] = time.perf_counter() - t0
+                        tp.close()
             except phi.PhiError as e:
                 rec["error"] = str(e)
             out.append(rec)

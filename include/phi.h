@@ -102,7 +102,13 @@ typedef struct {
   int32_t max_refine;       /* panel-count doublings allowed per tap chunk   */
   int32_t tile;             /* uv tile side used to sort visibilities (32)   */
   int32_t kernel_mode;      /* enum phi_kernel_mode                          */
-  int32_t reserved0;        /* must be 0                                     */
+  int32_t grid_staging;     /* PHI_KERNEL_TABLE only: 1 = one thread block per
+                               uv tile with its grid patch (tile + J_w cells
+                               a side) staged in shared memory, gridding
+                               privatised there and added to the grid once
+                               per tile; 0 = one warp per visibility reading
+                               the grid directly (default; as fast or faster
+                               on the workloads measured) */
   double oversample;        /* os; Npad = os * N must be an even integer     */
   double fov_rad;           /* full field of view in direction cosine        */
   double kmeans_tol;        /* Algorithm 1 convergence (default 1e-3)        */

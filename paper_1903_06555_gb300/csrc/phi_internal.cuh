@@ -44,6 +44,9 @@ __host__ __device__ inline int panel_count_for(float want) {
   return static_cast<int>(ceilf(want));
 }
 
+// Largest number of visibility records in one uv-tile work item.
+constexpr int kItemRecords = 128;
+
 // Panels evaluated per batch out of the per-warp shared node buffer.
 constexpr int kPanelBatch = 16;
 constexpr int kNodeBatch = 15 * kPanelBatch;
@@ -137,6 +140,15 @@ struct Plan {
   int64_t table_nr = 0, table_nw = 0;
   double table_hr = 0, table_hw = 0;
   std::vector<double> stack_maxabs;   // largest |w - wbar_k| of each stack's kept visibilities
+  // uv-tile work items (table path): item i covers sorted records
+  // [item_start[2 i], item_start[2 i + 1]), all in the uv tile item_key[i]
+  // (low 24 bits: tile_v * tiles_per_row + tile_u), at most kItemRecords
+  int32_t* item_start = nullptr;
+  uint32_t* item_key = nullptr;
+  std::vector<int64_t> stack_item_off;  // K + 1 offsets into the items
+  std::vector<uint8_t> stack_staged;    // table path: stage this stack's grid tiles
+  int tile = 32;
+  int tiles_per_row = 0;
 
   QuadParams quad() const {
     QuadParams q;

@@ -20,6 +20,7 @@
 // transpose pair exactly.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "bessel_j0.cuh"
@@ -376,18 +377,27 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
                                                      const C* __restrict__ vis_in,
                                                      C* __restrict__ vis_out, QuadParams q,
                                                      unsigned long long* head,
-                                                     unsigned long long* stats) {
+                                                     unsigned long long* stats, int batch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int npad = q.npad;
+  // visibilities are claimed `batch` at a time (one atomic per batch on the
+  // shared queue head)
+  const unsigned long long kBatch = static_cast<unsigned long long>(batch);
+  unsigned long long next = 0, stop = 0;
   while (true) {
-    unsigned long long i = 0;
-    if (lane == 0) i = atomicAdd(head, 1ULL);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= static_cast<unsigned long long>(n)) break;
+    if (next == stop) {
+      unsigned long long i0 = 0;
+      if (lane == 0) i0 = atomicAdd(head, kBatch);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+      next = i0;
+      stop = min(i0 + kBatch, static_cast<unsigned long long>(n));
+      if (next >= stop) break;
+    }
+    const unsigned long long i = next++;
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
     const int half = Jw / 2;
@@ -543,17 +553,27 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
                                                         C* grid_out, const C* __restrict__ vis_in,
                                                         C* __restrict__ vis_out, TableView<T> tv,
                                                         int npad_i, unsigned long long* head,
-                                                        unsigned long long* stats) {
+                                                        unsigned long long* stats, int batch) {
   const int lane = threadIdx.x & 31;
   const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
   const int npad = npad_i;
   const int nr = static_cast<int>(tv.nr), nw = static_cast<int>(tv.nw);
   unsigned long long my_taps = 0;
+  // Visibilities are claimed `batch` at a time: with small supports a
+  // visibility is cheap and one atomic per visibility on the shared queue
+  // head would serialise the warps.
+  const unsigned long long kBatch = static_cast<unsigned long long>(batch);
+  unsigned long long next = 0, stop = 0;
   while (true) {
-    unsigned long long i = 0;
-    if (lane == 0) i = atomicAdd(head, 1ULL);
-    i = __shfl_sync(0xffffffffu, i, 0);
-    if (i >= static_cast<unsigned long long>(n)) break;
+    if (next == stop) {
+      unsigned long long i0 = 0;
+      if (lane == 0) i0 = atomicAdd(head, kBatch);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+      next = i0;
+      stop = min(i0 + kBatch, static_cast<unsigned long long>(n));
+      if (next >= stop) break;
+    }
+    const unsigned long long i = next++;
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
     const int half = Jw / 2;
@@ -643,6 +663,145 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
   if (lane == 0 && my_taps) atomicAdd(stats + 1, my_taps);
 }
 
+// Degrid / grid with the tabulated kernel, one thread block per uv-tile work
+// item.  The block stages the item's grid patch -- the tile plus J_w - 1
+// cells of halo, wrapped circularly -- in shared memory: degridding reads
+// every tap from the patch; gridding accumulates into the zeroed patch with
+// shared-memory atomics and adds the patch to the grid once, with one global
+// atomic per non-zero cell instead of one per tap.
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256) tile_table_kernel(
+    const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm,
+    const int32_t* __restrict__ item_se, const uint32_t* __restrict__ item_key, int n_items,
+    const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
+    C* __restrict__ vis_out, TableView<T> tv, int npad, int tile, int tiles_per_row, int jmax,
+    unsigned long long* head, unsigned long long* stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* patch = reinterpret_cast<C*>(smem_raw);
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int side = tile + jmax;
+  const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
+  const int nr = static_cast<int>(tv.nr), nw = static_cast<int>(tv.nw);
+  const T last_r = static_cast<T>(nr - 2);
+  unsigned long long my_taps = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(head, 1ULL));
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const uint32_t key = item_key[item] & 0xffffffu;
+    const int tu = static_cast<int>(key % tiles_per_row), tvv = static_cast<int>(key / tiles_per_row);
+    const int u0 = tu * tile - npad / 2 - jmax / 2 + 1;
+    const int v0 = tvv * tile - npad / 2 - jmax / 2 + 1;
+    for (int c = threadIdx.x; c < side * side; c += blockDim.x) {
+      const int pv = c / side, pu = c - pv * side;
+      if (kGrid) {
+        patch[c] = cmake<C>(0.0, 0.0);
+      } else {
+        patch[c] = grid_in[static_cast<int64_t>(wrap_index(v0 + pv, npad)) * npad +
+                           wrap_index(u0 + pu, npad)];
+      }
+    }
+    __syncthreads();
+    const int r0 = item_se[2 * item], r1 = item_se[2 * item + 1];
+    for (int ri = r0 + warp; ri < r1; ri += nwarps) {
+      const VisRec<T> r = recs[ri];
+      const int Jw = r.jw;
+      const int half = Jw / 2;
+      const T aw = static_cast<T>(fabs(r.dw)) * tv.inv_hw;
+      const int jrow = aw < static_cast<T>(nw - 2) ? static_cast<int>(aw) : nw - 2;
+      const T fw = aw - static_cast<T>(jrow);
+      const bool neg = r.dw < 0.0;
+      const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
+      const uint32_t pm = perm[ri];
+      C yv = cmake<C>(0.0, 0.0);
+      if (kGrid) {
+        C v = vis_in[pm & 0x7fffffffu];
+        if (pm >> 31) v.y = -v.y;
+        yv.x = v.x * static_cast<T>(r.weight);
+        yv.y = v.y * static_cast<T>(r.weight);
+      }
+      // patch position of tap (0, 0) = (bu - half + 1, bv - half + 1)
+      const int pu0 = r.bu - half + 1 - u0, pv0 = r.bv - half + 1 - v0;
+      C accv = cmake<C>(0.0, 0.0);
+      const int ntap = Jw * Jw;
+      int a = lane % Jw, b = lane / Jw;
+      const int step_b = 32 / Jw, step_a = 32 % Jw;
+      T du_ = r.fu - static_cast<T>(a - half + 1), dv_ = r.fv - static_cast<T>(b - half + 1);
+      const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
+      const T fJw = static_cast<T>(Jw);
+      for (int t0 = 0; t0 < ntap; t0 += 32) {
+        if (t0 + lane < ntap) {
+          const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
+          int ir;
+          T fr;
+          table_index(sr, nr - 2, last_r, ir, fr);
+          const KPair<C> p0 = row[ir], p1 = row[ir + 1];
+          const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
+          const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
+          C K;
+          K.x = fma(fw, hi_x - lo_x, lo_x);
+          K.y = fma(fw, hi_y - lo_y, lo_y);
+          if (neg) K.y = -K.y;
+          ++my_taps;
+          const int li = (pv0 + b) * side + (pu0 + a);
+          if (kGrid) {
+            atomicAdd(&patch[li].x, K.x * yv.x + K.y * yv.y);   // conj(K) * yv
+            atomicAdd(&patch[li].y, K.x * yv.y - K.y * yv.x);
+          } else {
+            const C g = patch[li];
+            accv.x += K.x * g.x - K.y * g.y;
+            accv.y += K.x * g.y + K.y * g.x;
+          }
+        }
+        a += step_a;
+        b += step_b;
+        du_ -= fstep_a;
+        dv_ -= fstep_b;
+        if (a >= Jw) {
+          a -= Jw;
+          ++b;
+          du_ += fJw;
+          dv_ -= T(1);
+        }
+      }
+      if (!kGrid) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
+          accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
+        }
+        if (lane == 0) {
+          C out;
+          out.x = accv.x * static_cast<T>(r.weight);
+          out.y = accv.y * static_cast<T>(r.weight);
+          if (pm >> 31) out.y = -out.y;
+          vis_out[pm & 0x7fffffffu] = out;
+        }
+      }
+    }
+    __syncthreads();
+    if (kGrid) {
+      for (int c = threadIdx.x; c < side * side; c += blockDim.x) {
+        const C v = patch[c];
+        if (v.x != T(0) || v.y != T(0)) {
+          const int pv = c / side, pu = c - pv * side;
+          atomic_add_c(grid_out + static_cast<int64_t>(wrap_index(v0 + pv, npad)) * npad +
+                           wrap_index(u0 + pu, npad),
+                       v);
+        }
+      }
+      __syncthreads();
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
+  if (lane == 0 && my_taps) atomicAdd(stats + 1, my_taps);
+}
+
 // phi_wkernel: one warp per point, lane 0 carries the tap.
 template <typename T, typename C>
 __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__ rho_in,
@@ -724,6 +883,48 @@ TableView<T> table_view(const Plan& p) {
   return v;
 }
 
+// Visibilities a warp claims per queue atomic: about 1/32 of each warp's
+// share, so the queue head is not contended when visibilities are cheap and
+// the tail stays short when they are expensive.
+inline int queue_batch(int64_t n, int64_t warps) {
+  const int64_t b = n / (32 * (warps > 0 ? warps : 1));
+  return static_cast<int>(b < 1 ? 1 : (b > 64 ? 64 : b));
+}
+
+#define PHI_TRY_ST(expr)        \
+  do {                          \
+    int st_ = (expr);           \
+    if (st_ != PHI_OK) return st_; \
+  } while (0)
+
+// One launch over the uv-tile work items of stack k (records of the whole
+// plan are indexed directly: items hold absolute record ranges).
+template <typename T, typename C, bool kGrid>
+int launch_tile_table(Plan& p, int k, const C* grid_in, C* grid_out, const C* vis_in, C* vis_out,
+                      cudaStream_t s) {
+  const int64_t i0 = p.stack_item_off[k], ni = p.stack_item_off[k + 1] - i0;
+  if (ni == 0) return PHI_OK;
+  const int jmax = std::max(p.stack_jw[k], 2);
+  const int side = p.tile + jmax;
+  const size_t smem = sizeof(C) * static_cast<size_t>(side) * side;
+  PHI_CUDA_TRY(cudaFuncSetAttribute(tile_table_kernel<T, C, kGrid>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_table_kernel<T, C, kGrid>,
+                                                    kVisThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t want = static_cast<int64_t>(per_sm) * p.num_sms;
+  const int blocks = static_cast<int>(ni < want ? ni : want);
+  tile_table_kernel<T, C, kGrid><<<blocks, kVisThreads, smem, s>>>(
+      static_cast<const VisRec<T>*>(p.recs), p.perm, p.item_start + 2 * i0, p.item_key + i0,
+      static_cast<int>(ni), grid_in, grid_out, vis_in, vis_out, table_view<T, C>(p), p.npad,
+      p.tile, p.tiles_per_row, jmax, p.counters + k, p.counters + p.K);
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
 template <typename T, typename C>
 int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
   const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
@@ -755,14 +956,17 @@ int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
     if (fr != CUFFT_SUCCESS) return PHI_ERR_CUDA;
     timer_end(p, ev, PHI_STAGE_FFT, s);
     ev = timer_begin(p, s);
-    if (p.d.kernel_mode == PHI_KERNEL_TABLE)
+    if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.stack_staged[k])
+      PHI_TRY_ST((launch_tile_table<T, C, false>(p, k, grid, nullptr, nullptr, y, s)));
+    else if (p.d.kernel_mode == PHI_KERNEL_TABLE)
       vis_table_kernel<T, C, false><<<p.num_sms * 8, kVisThreads, 0, s>>>(
           static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y,
-          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K);
+          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K,
+          queue_batch(nk, p.num_sms * 8 * (kVisThreads / 32)));
     else
       vis_kernel<T, C, false><<<vis_blocks, kVisThreads, smem, s>>>(
           static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y,
-          q, p.counters + k, p.counters + p.K);
+          q, p.counters + k, p.counters + p.K, queue_batch(nk, vis_blocks * (kVisThreads / 32)));
     PHI_CUDA_TRY(cudaGetLastError());
     timer_end(p, ev, PHI_STAGE_DEGRID, s);
   }
@@ -785,14 +989,17 @@ int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
     PHI_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * (size_t)p.npad * p.npad, s));
     timer_end(p, ev, PHI_STAGE_CLEAR, s);
     ev = timer_begin(p, s);
-    if (p.d.kernel_mode == PHI_KERNEL_TABLE)
+    if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.stack_staged[k])
+      PHI_TRY_ST((launch_tile_table<T, C, true>(p, k, nullptr, grid, y, nullptr, s)));
+    else if (p.d.kernel_mode == PHI_KERNEL_TABLE)
       vis_table_kernel<T, C, true><<<p.num_sms * 8, kVisThreads, 0, s>>>(
           static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr,
-          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K);
+          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K,
+          queue_batch(nk, p.num_sms * 8 * (kVisThreads / 32)));
     else
       vis_kernel<T, C, true><<<vis_blocks, kVisThreads, smem, s>>>(
           static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr,
-          q, p.counters + k, p.counters + p.K);
+          q, p.counters + k, p.counters + p.K, queue_batch(nk, vis_blocks * (kVisThreads / 32)));
     PHI_CUDA_TRY(cudaGetLastError());
     timer_end(p, ev, PHI_STAGE_GRID, s);
     ev = timer_begin(p, s);

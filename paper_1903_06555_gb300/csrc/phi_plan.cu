@@ -7,6 +7,7 @@
 // deterministically (fixed block ranges, warp butterflies, fixed-order
 // combination), so a plan is bit-reproducible run to run.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -228,6 +229,27 @@ __global__ void records_kernel(const double* __restrict__ uvw, const uint8_t* __
   }
 }
 
+// Tile segmentation of the sorted records: flag the first record of each
+// (stack, tile) key, then scatter the starts and keys of the tiles.
+__global__ void tile_flag_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                 uint32_t* __restrict__ flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    flag[i] = (i == 0 || keys[i] != keys[i - 1]) ? 1u : 0u;
+}
+
+__global__ void tile_scatter_kernel(const uint32_t* __restrict__ keys,
+                                    const uint32_t* __restrict__ flag,
+                                    const uint32_t* __restrict__ pos, int64_t n,
+                                    int32_t* __restrict__ start, uint32_t* __restrict__ key) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) {
+      start[pos[i]] = static_cast<int32_t>(i);
+      key[pos[i]] = keys[i];
+    }
+}
+
 struct Scratch {
   std::vector<void*> ptrs;
   ~Scratch() {
@@ -261,6 +283,8 @@ void free_plan(Plan* p) {
   cudaFree(p->grid);
   cudaFree(p->counters);
   cudaFree(p->table);
+  cudaFree(p->item_start);
+  cudaFree(p->item_key);
 }
 
 template <typename X>
@@ -300,7 +324,8 @@ int validate(const phi_plan_desc& d, int64_t M) {
   if (d.tile < 0 || d.tile > 4096) return PHI_ERR_ARG;
   if (d.kb_beta < 0.0 || d.cycles_per_panel < 0.0) return PHI_ERR_ARG;
   if (d.kernel_mode != PHI_KERNEL_QUADRATURE && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
-  if (d.reserved0 != 0) return PHI_ERR_ARG;
+  if (d.grid_staging != 0 && d.grid_staging != 1) return PHI_ERR_ARG;
+  if (d.grid_staging && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
   if (d.kernel_mode == PHI_KERNEL_TABLE && !(d.table_tol > 0.0 && d.table_tol < 1.0))
     return PHI_ERR_ARG;
   return PHI_OK;
@@ -528,6 +553,78 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
     PHI_CUDA_TRY(cudaGetLastError());
   }
 
+  // --- uv-tile work items for the table path: tiles of the sorted kept
+  // records, split into items of at most kItemRecords records
+  p.tile = tile;
+  p.tiles_per_row = tiles_per_row;
+  p.stack_item_off.assign(K + 1, 0);
+  p.stack_staged.assign(K, 0);
+  if (d.kernel_mode == PHI_KERNEL_TABLE && d.grid_staging && p.n_kept > 0) {
+    const int64_t n = p.n_kept;
+    uint32_t *flag = nullptr, *pos = nullptr, *tkey = nullptr;
+    int32_t* tstart = nullptr;
+    PHI_CUDA_TRY(tmp.alloc(&flag, n));
+    PHI_CUDA_TRY(tmp.alloc(&pos, n));
+    PHI_CUDA_TRY(tmp.alloc(&tkey, n));
+    PHI_CUDA_TRY(tmp.alloc(&tstart, n));
+    tile_flag_kernel<<<nblk, kPlanThreads, 0, s>>>(skeys, n, flag);
+    PHI_CUDA_TRY(cudaGetLastError());
+    size_t scan_bytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, flag, pos, static_cast<int>(n), s);
+    void* scan_tmp = nullptr;
+    PHI_CUDA_TRY(tmp.alloc(reinterpret_cast<unsigned char**>(&scan_tmp), scan_bytes));
+    if (cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, flag, pos, static_cast<int>(n), s) !=
+        cudaSuccess)
+      return PHI_ERR_CUDA;
+    tile_scatter_kernel<<<nblk, kPlanThreads, 0, s>>>(skeys, flag, pos, n, tstart, tkey);
+    PHI_CUDA_TRY(cudaGetLastError());
+    uint32_t last[2] = {0, 0};
+    PHI_CUDA_TRY(cudaMemcpyAsync(&last[0], pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaMemcpyAsync(&last[1], flag + n - 1, 4, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+    const int64_t n_tiles = static_cast<int64_t>(last[0]) + last[1];
+    std::vector<int32_t> hstart(n_tiles + 1);
+    std::vector<uint32_t> hkey(n_tiles);
+    PHI_CUDA_TRY(cudaMemcpyAsync(hstart.data(), tstart, 4 * n_tiles, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaMemcpyAsync(hkey.data(), tkey, 4 * n_tiles, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+    hstart[n_tiles] = static_cast<int32_t>(n);
+    std::vector<int32_t> istart;
+    std::vector<uint32_t> ikey;
+    int cur_stack = -1;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+      const int st = static_cast<int>(hkey[t] >> 24);
+      while (cur_stack < st) p.stack_item_off[++cur_stack] = static_cast<int64_t>(ikey.size());
+      for (int32_t r = hstart[t]; r < hstart[t + 1]; r += kItemRecords) {
+        istart.push_back(r);
+        ikey.push_back(hkey[t]);
+      }
+    }
+    while (cur_stack < K) p.stack_item_off[++cur_stack] = static_cast<int64_t>(ikey.size());
+    istart.push_back(static_cast<int32_t>(n));
+    // item i ends where item i + 1 starts, or at its tile's end for the last
+    // item of a tile: record the ends via the next start, fixing tile ends
+    std::vector<int32_t> iend(ikey.size());
+    {
+      size_t i = 0;
+      for (int64_t t = 0; t < n_tiles; ++t)
+        for (int32_t r = hstart[t]; r < hstart[t + 1]; r += kItemRecords, ++i)
+          iend[i] = std::min<int32_t>(r + kItemRecords, hstart[t + 1]);
+    }
+    // store start and end interleaved: item_start[2 i] = start, [2 i + 1] = end
+    std::vector<int32_t> se(2 * ikey.size());
+    for (size_t i = 0; i < ikey.size(); ++i) {
+      se[2 * i] = istart[i];
+      se[2 * i + 1] = iend[i];
+    }
+    for (int q = 0; q < K; ++q) p.stack_staged[q] = 1;
+    PHI_CUDA_TRY(owned_alloc(p, &p.item_start, se.size()));
+    PHI_CUDA_TRY(owned_alloc(p, &p.item_key, ikey.size()));
+    PHI_CUDA_TRY(cudaMemcpyAsync(p.item_start, se.data(), 4 * se.size(), cudaMemcpyHostToDevice, s));
+    PHI_CUDA_TRY(cudaMemcpyAsync(p.item_key, ikey.data(), 4 * ikey.size(), cudaMemcpyHostToDevice, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+
   // --- tables, grid, FFT plan
   const size_t tsize = f64 ? sizeof(double) : sizeof(float);
   const int64_t nodes = panel_table_offset(kMaxPanels + 1);
@@ -592,6 +689,7 @@ extern "C" int phi_plan_desc_default(phi_plan_desc* d) {
   d->kb_beta = 0.0;
   d->cycles_per_panel = 0.0;
   d->kernel_mode = PHI_KERNEL_QUADRATURE;
+  d->grid_staging = 0;
   d->table_tol = 1e-4;
   return PHI_OK;
 }

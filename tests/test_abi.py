@@ -89,6 +89,7 @@ def test_defaults_and_error_strings():
     assert d.quad_rel_tol == 1e-6 and d.quad_abs_tol == 1e-6 and d.alpha == 1.0
     assert d.max_support == 64 and d.precision == phi.PHI_F32
     assert d.kernel_mode == phi.PHI_KERNEL_QUADRATURE and d.table_tol == 1e-4
+    assert d.grid_staging == 0
     L = phi.lib()
     assert L.phi_error_string(0) == b"ok"
     for s in range(1, 8):
@@ -99,7 +100,8 @@ def test_defaults_and_error_strings():
 BAD = [dict(image_n=127), dict(image_n=0), dict(support=3), dict(n_stacks=0),
        dict(n_stacks=200), dict(precision=5), dict(oversample=1.25), dict(fov_rad=-1.0),
        dict(max_support=2), dict(quad_rel_tol=0.0), dict(support_rule=3), dict(max_refine=-1),
-       dict(kernel_mode=2), dict(kernel_mode=1, table_tol=0.0), dict(reserved0=1)]
+       dict(kernel_mode=2), dict(kernel_mode=1, table_tol=0.0), dict(grid_staging=2),
+       dict(grid_staging=1)]
 
 
 @pytest.mark.parametrize("bad", BAD)

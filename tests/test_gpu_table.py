@@ -31,11 +31,11 @@ def case():
                 y_ref=O.degrid_table(op, x, tab), x_ref=O.grid_table(op, yr, tab))
 
 
-def plan_for(c, precision):
+def plan_for(c, precision, staging=0):
     tol = 1e-12 if precision == "f64" else 1e-6
     return phi.Plan(torch.from_numpy(c["uvw"]), image_n=128, fov_rad=c["geo"].fov, n_stacks=3,
                     conj_fold=1, precision=precision, quad_rel_tol=tol, quad_abs_tol=tol,
-                    kernel_mode="table", table_tol=TABLE_TOL)
+                    kernel_mode="table", table_tol=TABLE_TOL, grid_staging=staging)
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
@@ -47,9 +47,10 @@ def test_table_geometry_matches_oracle(case, precision):
     assert abs(info["table_h_rho"] - tab.hr) < 1e-15 and abs(info["table_h_w"] - tab.hw) < 1e-15
 
 
+@pytest.mark.parametrize("staging", [0, 1])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_table_degrid_and_grid_match_oracle(case, precision):
-    plan = plan_for(case, precision)
+def test_table_degrid_and_grid_match_oracle(case, precision, staging):
+    plan = plan_for(case, precision, staging)
     rd = torch.float64 if precision == "f64" else torch.float32
     cd = torch.complex128 if precision == "f64" else torch.complex64
     tol = 1e-10 if precision == "f64" else 1e-5
