@@ -40,8 +40,8 @@
  *
  * Memory and streams: every pointer argument named *_dev is a device pointer
  * owned by the caller; the plan owns everything it allocates (sorted
- * visibility records, permutation, stack tables, per-pixel factors, one
- * padded grid, a cuFFT plan and its workspace).  Calls are asynchronous on the
+ * visibility records, permutation, stack tables, per-pixel factors, the
+ * padded grids of one group of stacks, cuFFT plans and their workspace).  Calls are asynchronous on the
  * given stream (a cudaStream_t passed as void*; NULL = legacy default stream)
  * and do not synchronise, except phi_plan_create (it reads the k-means
  * convergence test back every sweep) and the calls that return host values
@@ -101,6 +101,9 @@ typedef struct {
   int32_t support_rule;     /* enum phi_support_rule                         */
   int32_t max_refine;       /* panel-count doublings allowed per tap chunk   */
   int32_t tile;             /* uv tile side used to sort visibilities (32)   */
+  int32_t max_grid_mib;     /* device memory for the padded grids of stacks
+                               processed together (0: 4096 MiB); at least
+                               one grid is always held                      */
   int32_t kernel_mode;      /* enum phi_kernel_mode                          */
   int32_t grid_staging;     /* PHI_KERNEL_TABLE only: 1 = one thread block per
                                uv tile with its grid patch (tile + J_w cells
@@ -109,6 +112,7 @@ typedef struct {
                                per tile; 0 = one warp per visibility reading
                                the grid directly (default; as fast or faster
                                on the workloads measured) */
+  int32_t reserved0;        /* must be 0                                     */
   double oversample;        /* os; Npad = os * N must be an even integer     */
   double fov_rad;           /* full field of view in direction cosine        */
   double kmeans_tol;        /* Algorithm 1 convergence (default 1e-3)        */
@@ -132,7 +136,7 @@ typedef struct {
   int32_t image_n, npad, n_stacks, kmeans_sweeps, max_jw, precision;
   double du, dl, beta, window_radius, support_coeff;
   int32_t kernel_mode;      /* enum phi_kernel_mode                          */
-  int32_t reserved0;
+  int32_t group;            /* stacks whose grids are processed together     */
   int64_t table_n_rho;      /* PHI_KERNEL_TABLE: samples in rho (0 otherwise) */
   int64_t table_n_w;        /* samples in |w|                                */
   double table_h_rho;       /* spacing in grid pixels                        */

@@ -49,8 +49,10 @@ class PlanDesc(ctypes.Structure):
         ("support_rule", ctypes.c_int32),
         ("max_refine", ctypes.c_int32),
         ("tile", ctypes.c_int32),
+        ("max_grid_mib", ctypes.c_int32),
         ("kernel_mode", ctypes.c_int32),
         ("grid_staging", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
         ("oversample", ctypes.c_double),
         ("fov_rad", ctypes.c_double),
         ("kmeans_tol", ctypes.c_double),
@@ -82,7 +84,7 @@ class PlanSummary(ctypes.Structure):
         ("window_radius", ctypes.c_double),
         ("support_coeff", ctypes.c_double),
         ("kernel_mode", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("group", ctypes.c_int32),
         ("table_n_rho", ctypes.c_int64),
         ("table_n_w", ctypes.c_int64),
         ("table_h_rho", ctypes.c_double),

@@ -13,7 +13,9 @@
 //                       Gauss weights w) at the 15 P Gauss-Kronrod nodes;
 //   tap order           per even support J_w, its J_w^2 taps sorted by
 //                       distance from the box centre (uint16 a | b << 8);
-//   grid[Npad*Npad]     one padded complex grid reused by every stack;
+//   grids               padded complex grids of one group of stacks at a
+//                       time (as many as fit max_grid_mib), reused by every
+//                       group;
 //   counters            work-queue heads and quadrature statistics.
 #pragma once
 
@@ -64,7 +66,8 @@ struct __align__(16) VisRec<float> {
   int32_t bu, bv;    // floor(u/du), floor(v/du)
   double dw;         // w - wbar_k (FP64: it multiplies the chirp phase)
   float weight;      // W_i
-  int32_t jw;        // support J_w (even)
+  uint16_t jw;       // support J_w (even, <= 256)
+  uint16_t stack;    // w-stack k
 };
 
 template <>
@@ -74,7 +77,7 @@ struct __align__(16) VisRec<double> {
   double weight;
   int32_t bu, bv;
   int32_t jw;
-  int32_t pad;
+  int32_t stack;
 };
 
 // Shared per-node integrand values of one visibility, with the Kronrod
@@ -120,7 +123,15 @@ struct Plan {
   void* node_hd = nullptr;
   uint16_t* tap_order = nullptr;
   int32_t* tap_off = nullptr;
-  void* grid = nullptr;
+  void* grid = nullptr;                // group * Npad^2 complex: grids of one stack group
+  int group = 1;                        // stacks whose grids are resident together
+  std::vector<int64_t> group_off;       // groups: stacks group_stacks[group_off[g] .. group_off[g+1])
+  std::vector<int32_t> group_stacks;    // the stacks with visibilities, in order
+  int32_t* group_stacks_dev = nullptr;
+  int32_t* stack_slot_dev = nullptr;    // slot of each stack within its group
+  double* wbar_dev = nullptr;
+  cufftHandle fft_batch = 0;            // `group` transforms in one call
+  bool fft_batch_ok = false;
   // [0..K) work heads, [K] unconverged taps, [K+1] taps, [K+2] wkernel misses,
   // [K+3] tap-node evaluations
   unsigned long long* counters = nullptr;

@@ -212,60 +212,72 @@ int launch_pixel_tables(Plan& p, cudaStream_t s) {
 // Image-domain steps
 // ---------------------------------------------------------------------------
 
-// S~_k then Z: grid index j (row-major Npad^2) holds padded pixel
-// P = (j + Npad/2) mod Npad (centred image moved to index 0), i.e. image
-// pixel P - (Npad - N)/2, or zero outside the image.
+// S~_k then Z for every stack of a group (blockIdx.y = slot): grid cell
+// (qv, qu) holds padded pixel P = (q + Npad/2) mod Npad (the centred image
+// moved to index 0), i.e. image pixel P - (Npad - N)/2, or zero outside.
 template <typename T, typename C>
 __global__ void prep_kernel(const T* __restrict__ x, const double* __restrict__ omn,
-                            const T* __restrict__ corr, int N, int npad, double wbar,
-                            C* __restrict__ grid) {
-  int64_t total = (int64_t)npad * npad;
-  int off = (npad - N) / 2;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    int qv = static_cast<int>(j / npad), qu = static_cast<int>(j % npad);
+                            const T* __restrict__ corr, int N, int npad,
+                            const double* __restrict__ wbar, const int32_t* __restrict__ stacks,
+                            C* __restrict__ grids) {
+  const int off = (npad - N) / 2;
+  const double wb = wbar[stacks[blockIdx.y]];
+  C* grid = grids + static_cast<int64_t>(blockIdx.y) * npad * npad;
+  for (int qv = blockIdx.x; qv < npad; qv += gridDim.x) {
     int pv = qv + npad / 2;
     if (pv >= npad) pv -= npad;
-    int pu = qu + npad / 2;
-    if (pu >= npad) pu -= npad;
     pv -= off;
-    pu -= off;
-    C out = cmake<C>(0.0, 0.0);
-    if (pv >= 0 && pv < N && pu >= 0 && pu < N) {
-      int64_t pix = (int64_t)pv * N + pu;
-      double t = wbar * omn[pix];
-      t -= rint(t);
-      T sn, cs;
-      sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
-      T v = x[pix] * corr[pix];
-      out.x = v * cs;
-      out.y = v * sn;
+    const bool row_in = pv >= 0 && pv < N;
+    for (int qu = threadIdx.x; qu < npad; qu += blockDim.x) {
+      int pu = qu + npad / 2;
+      if (pu >= npad) pu -= npad;
+      pu -= off;
+      C out = cmake<C>(0.0, 0.0);
+      if (row_in && pu >= 0 && pu < N) {
+        const int64_t pix = static_cast<int64_t>(pv) * N + pu;
+        double t = wb * omn[pix];
+        t -= rint(t);
+        T sn, cs;
+        sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
+        const T v = x[pix] * corr[pix];
+        out.x = v * cs;
+        out.y = v * sn;
+      }
+      grid[static_cast<int64_t>(qv) * npad + qu] = out;
     }
-    grid[j] = out;
   }
 }
 
-// After the inverse FFT: x_p (+)= Re(conj(S~_k) G[P(p)]).
+// After the inverse FFTs of a group: x_p (+)= sum over its stacks of
+// Re(conj(S~_k) G_k[P(p)]), one pass over the image per group.
 template <typename T, typename C>
-__global__ void finish_kernel(const C* __restrict__ grid, const double* __restrict__ omn,
-                              const T* __restrict__ corr, int N, int npad, double wbar,
-                              T* __restrict__ x, int accumulate) {
-  int64_t total = (int64_t)N * N;
-  int off = (npad - N) / 2;
-  for (int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pix < total;
-       pix += (int64_t)gridDim.x * blockDim.x) {
-    int pv = static_cast<int>(pix / N), pu = static_cast<int>(pix % N);
+__global__ void finish_kernel(const C* __restrict__ grids, const double* __restrict__ omn,
+                              const T* __restrict__ corr, int N, int npad,
+                              const double* __restrict__ wbar, const int32_t* __restrict__ stacks,
+                              int nslots, T* __restrict__ x, int accumulate) {
+  const int off = (npad - N) / 2;
+  const int64_t plane = static_cast<int64_t>(npad) * npad;
+  for (int pv = blockIdx.x; pv < N; pv += gridDim.x) {
     int qv = pv + off + npad / 2;
     if (qv >= npad) qv -= npad;
-    int qu = pu + off + npad / 2;
-    if (qu >= npad) qu -= npad;
-    C g = grid[(int64_t)qv * npad + qu];
-    double t = wbar * omn[pix];
-    t -= rint(t);
-    T sn, cs;
-    sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
-    T v = corr[pix] * (cs * g.x + sn * g.y);
-    x[pix] = accumulate ? x[pix] + v : v;
+    for (int pu = threadIdx.x; pu < N; pu += blockDim.x) {
+      int qu = pu + off + npad / 2;
+      if (qu >= npad) qu -= npad;
+      const int64_t pix = static_cast<int64_t>(pv) * N + pu;
+      const int64_t gi = static_cast<int64_t>(qv) * npad + qu;
+      const double om = omn[pix];
+      T acc = 0;
+      for (int sl = 0; sl < nslots; ++sl) {
+        const C g = grids[sl * plane + gi];
+        double t = wbar[stacks[sl]] * om;
+        t -= rint(t);
+        T sn, cs;
+        sincos_pi(static_cast<T>(2.0 * t), &sn, &cs);
+        acc += cs * g.x + sn * g.y;
+      }
+      const T v = corr[pix] * acc;
+      x[pix] = accumulate ? x[pix] + v : v;
+    }
   }
 }
 
@@ -376,6 +388,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
                                                      const C* __restrict__ grid_in, C* grid_out,
                                                      const C* __restrict__ vis_in,
                                                      C* __restrict__ vis_out, QuadParams q,
+                                                     const int32_t* __restrict__ stack_slot,
                                                      unsigned long long* head,
                                                      unsigned long long* stats, int batch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -400,6 +413,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
     const unsigned long long i = next++;
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
+    // the grid of this visibility's stack within the resident group
+    const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
     const int half = Jw / 2;
     const T fu = r.fu, fv = r.fv;
     const uint16_t* order = q.tap_order + q.tap_off[half - 1];
@@ -432,7 +447,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
       if (active) {
         ++my_taps;
         if (!ok) ++my_bad;
-        const int64_t gi = static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
         if (kGrid) {
           C add;
@@ -552,7 +567,9 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
                                                         int64_t n, const C* __restrict__ grid_in,
                                                         C* grid_out, const C* __restrict__ vis_in,
                                                         C* __restrict__ vis_out, TableView<T> tv,
-                                                        int npad_i, unsigned long long* head,
+                                                        int npad_i,
+                                                        const int32_t* __restrict__ stack_slot,
+                                                        unsigned long long* head,
                                                         unsigned long long* stats, int batch) {
   const int lane = threadIdx.x & 31;
   const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
@@ -576,6 +593,8 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
     const unsigned long long i = next++;
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
+    // the grid of this visibility's stack within the resident group
+    const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
     const int half = Jw / 2;
     const T fu = r.fu, fv = r.fv;
     const T aw = static_cast<T>(fabs(r.dw)) * tv.inv_hw;
@@ -619,7 +638,7 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
         K.y = fma(fw, hi_y - lo_y, lo_y);
         if (neg) K.y = -K.y;
         ++my_taps;
-        const int64_t gi = static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
         if (kGrid) {
           C add;
@@ -673,9 +692,9 @@ template <typename T, typename C, bool kGrid>
 __global__ void __launch_bounds__(256) tile_table_kernel(
     const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm,
     const int32_t* __restrict__ item_se, const uint32_t* __restrict__ item_key, int n_items,
-    const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
+    const C* __restrict__ grids_in, C* grids_out, const C* __restrict__ vis_in,
     C* __restrict__ vis_out, TableView<T> tv, int npad, int tile, int tiles_per_row, int jmax,
-    unsigned long long* head, unsigned long long* stats) {
+    const int32_t* __restrict__ stack_slot, unsigned long long* head, unsigned long long* stats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* patch = reinterpret_cast<C*>(smem_raw);
   __shared__ int s_item;
@@ -692,6 +711,10 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
     __syncthreads();
     const int item = s_item;
     if (item >= n_items) break;
+    const int64_t gbase =
+        static_cast<int64_t>(stack_slot[item_key[item] >> 24]) * npad * npad;
+    const C* __restrict__ grid_in = kGrid ? nullptr : grids_in + gbase;
+    C* grid_out = kGrid ? grids_out + gbase : nullptr;
     const uint32_t key = item_key[item] & 0xffffffu;
     const int tu = static_cast<int>(key % tiles_per_row), tvv = static_cast<int>(key / tiles_per_row);
     const int u0 = tu * tile - npad / 2 - jmax / 2 + 1;
@@ -897,11 +920,11 @@ inline int queue_batch(int64_t n, int64_t warps) {
     if (st_ != PHI_OK) return st_; \
   } while (0)
 
-// One launch over the uv-tile work items of stack k (records of the whole
-// plan are indexed directly: items hold absolute record ranges).
+// One launch over the uv-tile work items of stack k (items hold absolute
+// record ranges; each item finds its stack's grid in the group by its key).
 template <typename T, typename C, bool kGrid>
-int launch_tile_table(Plan& p, int k, const C* grid_in, C* grid_out, const C* vis_in, C* vis_out,
-                      cudaStream_t s) {
+int launch_tile_table(Plan& p, int k, const C* grids_in, C* grids_out, const C* vis_in,
+                      C* vis_out, cudaStream_t s) {
   const int64_t i0 = p.stack_item_off[k], ni = p.stack_item_off[k + 1] - i0;
   if (ni == 0) return PHI_OK;
   const int jmax = std::max(p.stack_jw[k], 2);
@@ -919,55 +942,88 @@ int launch_tile_table(Plan& p, int k, const C* grid_in, C* grid_out, const C* vi
   const int blocks = static_cast<int>(ni < want ? ni : want);
   tile_table_kernel<T, C, kGrid><<<blocks, kVisThreads, smem, s>>>(
       static_cast<const VisRec<T>*>(p.recs), p.perm, p.item_start + 2 * i0, p.item_key + i0,
-      static_cast<int>(ni), grid_in, grid_out, vis_in, vis_out, table_view<T, C>(p), p.npad,
-      p.tile, p.tiles_per_row, jmax, p.counters + k, p.counters + p.K);
+      static_cast<int>(ni), grids_in, grids_out, vis_in, vis_out, table_view<T, C>(p), p.npad,
+      p.tile, p.tiles_per_row, jmax, p.stack_slot_dev, p.counters + k, p.counters + p.K);
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
+// In-place FFTs of the first n grids of the group (one batched call when
+// the group is full).
+template <typename T, typename C>
+int fft_group(Plan& p, C* grids, int n, int dir, cudaStream_t s) {
+  const int64_t plane = static_cast<int64_t>(p.npad) * p.npad;
+  auto run = [&](cufftHandle h, C* g) -> cufftResult {
+    if (cufftSetStream(h, s) != CUFFT_SUCCESS) return CUFFT_EXEC_FAILED;
+    if (sizeof(T) == 8)
+      return cufftExecZ2Z(h, reinterpret_cast<cufftDoubleComplex*>(g),
+                          reinterpret_cast<cufftDoubleComplex*>(g), dir);
+    return cufftExecC2C(h, reinterpret_cast<cufftComplex*>(g), reinterpret_cast<cufftComplex*>(g),
+                        dir);
+  };
+  if (n == p.group && p.fft_batch_ok) {
+    if (run(p.fft_batch, grids) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+  } else {
+    for (int i = 0; i < n; ++i)
+      if (run(p.fft, grids + i * plane) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+  }
+  return PHI_OK;
+}
+
+// The fused kernel over all records of the group's stacks (contiguous in
+// the sorted order).
+template <typename T, typename C, bool kGrid>
+int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C* vis_in,
+                        C* vis_out, cudaStream_t s) {
+  const int64_t s0 = p.group_off[g], s1 = p.group_off[g + 1];
+  if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.d.grid_staging) {
+    for (int64_t i = s0; i < s1; ++i)
+      PHI_TRY_ST((launch_tile_table<T, C, kGrid>(p, p.group_stacks[i], grids_in, grids_out, vis_in,
+                                                 vis_out, s)));
+    return PHI_OK;
+  }
+  const int64_t b0 = p.stack_off[p.group_stacks[s0]];
+  const int64_t nk = p.stack_off[p.group_stacks[s1 - 1] + 1] - b0;
+  if (nk == 0) return PHI_OK;
+  const VisRec<T>* recs = static_cast<const VisRec<T>*>(p.recs) + b0;
+  if (p.d.kernel_mode == PHI_KERNEL_TABLE) {
+    const int blocks = p.num_sms * 8;
+    vis_table_kernel<T, C, kGrid><<<blocks, kVisThreads, 0, s>>>(
+        recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, table_view<T, C>(p), p.npad,
+        p.stack_slot_dev, p.counters + g, p.counters + p.K,
+        queue_batch(nk, blocks * (kVisThreads / 32)));
+  } else {
+    const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
+    const int blocks = blocks_for_vis<T, C>(p, smem);
+    vis_kernel<T, C, kGrid><<<blocks, kVisThreads, smem, s>>>(
+        recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(), p.stack_slot_dev,
+        p.counters + g, p.counters + p.K, queue_batch(nk, blocks * (kVisThreads / 32)));
+  }
   PHI_CUDA_TRY(cudaGetLastError());
   return PHI_OK;
 }
 
 template <typename T, typename C>
 int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
-  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
   long ev = timer_begin(p, s);
   PHI_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(C) * (size_t)p.M, s));
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
   timer_end(p, ev, PHI_STAGE_CLEAR, s);
-  const int vis_blocks = blocks_for_vis<T, C>(p, smem);
-  const int img_blocks = p.num_sms * 8;
-  const QuadParams q = p.quad();
-  C* grid = static_cast<C*>(p.grid);
-  for (int k = 0; k < p.K; ++k) {
-    const int64_t b0 = p.stack_off[k], nk = p.stack_off[k + 1] - b0;
-    if (nk == 0) continue;
+  C* grids = static_cast<C*>(p.grid);
+  const int ngroups = static_cast<int>(p.group_off.size()) - 1;
+  for (int g = 0; g < ngroups; ++g) {
+    const int n = static_cast<int>(p.group_off[g + 1] - p.group_off[g]);
     ev = timer_begin(p, s);
-    prep_kernel<T, C><<<img_blocks, 256, 0, s>>>(x, p.omn_pix, static_cast<const T*>(p.corr_pix),
-                                                 p.N, p.npad, p.wbar[k], grid);
+    prep_kernel<T, C><<<dim3(p.num_sms * 4, n), 256, 0, s>>>(
+        x, p.omn_pix, static_cast<const T*>(p.corr_pix), p.N, p.npad, p.wbar_dev,
+        p.group_stacks_dev + p.group_off[g], grids);
     PHI_CUDA_TRY(cudaGetLastError());
     timer_end(p, ev, PHI_STAGE_PREP, s);
     ev = timer_begin(p, s);
-    if (cufftSetStream(p.fft, s) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
-    cufftResult fr;
-    if (sizeof(T) == 8)
-      fr = cufftExecZ2Z(p.fft, reinterpret_cast<cufftDoubleComplex*>(grid),
-                        reinterpret_cast<cufftDoubleComplex*>(grid), CUFFT_FORWARD);
-    else
-      fr = cufftExecC2C(p.fft, reinterpret_cast<cufftComplex*>(grid),
-                        reinterpret_cast<cufftComplex*>(grid), CUFFT_FORWARD);
-    if (fr != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    PHI_TRY_ST((fft_group<T, C>(p, grids, n, CUFFT_FORWARD, s)));
     timer_end(p, ev, PHI_STAGE_FFT, s);
     ev = timer_begin(p, s);
-    if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.stack_staged[k])
-      PHI_TRY_ST((launch_tile_table<T, C, false>(p, k, grid, nullptr, nullptr, y, s)));
-    else if (p.d.kernel_mode == PHI_KERNEL_TABLE)
-      vis_table_kernel<T, C, false><<<p.num_sms * 8, kVisThreads, 0, s>>>(
-          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y,
-          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K,
-          queue_batch(nk, p.num_sms * 8 * (kVisThreads / 32)));
-    else
-      vis_kernel<T, C, false><<<vis_blocks, kVisThreads, smem, s>>>(
-          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grid, nullptr, nullptr, y,
-          q, p.counters + k, p.counters + p.K, queue_batch(nk, vis_blocks * (kVisThreads / 32)));
-    PHI_CUDA_TRY(cudaGetLastError());
+    PHI_TRY_ST((launch_group_kernel<T, C, false>(p, g, grids, nullptr, nullptr, y, s)));
     timer_end(p, ev, PHI_STAGE_DEGRID, s);
   }
   return PHI_OK;
@@ -975,53 +1031,29 @@ int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
 
 template <typename T, typename C>
 int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
-  const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
-  const int vis_blocks = blocks_for_vis<T, C>(p, smem);
-  const int img_blocks = p.num_sms * 8;
-  const QuadParams q = p.quad();
-  C* grid = static_cast<C*>(p.grid);
-  bool first = true;
-  for (int k = 0; k < p.K; ++k) {
-    const int64_t b0 = p.stack_off[k], nk = p.stack_off[k + 1] - b0;
-    if (nk == 0) continue;
+  C* grids = static_cast<C*>(p.grid);
+  const int64_t plane = static_cast<int64_t>(p.npad) * p.npad;
+  const int ngroups = static_cast<int>(p.group_off.size()) - 1;
+  for (int g = 0; g < ngroups; ++g) {
+    const int n = static_cast<int>(p.group_off[g + 1] - p.group_off[g]);
     long ev = timer_begin(p, s);
-    PHI_CUDA_TRY(cudaMemsetAsync(grid, 0, sizeof(C) * (size_t)p.npad * p.npad, s));
+    PHI_CUDA_TRY(cudaMemsetAsync(grids, 0, sizeof(C) * plane * n, s));
     timer_end(p, ev, PHI_STAGE_CLEAR, s);
     ev = timer_begin(p, s);
-    if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.stack_staged[k])
-      PHI_TRY_ST((launch_tile_table<T, C, true>(p, k, nullptr, grid, y, nullptr, s)));
-    else if (p.d.kernel_mode == PHI_KERNEL_TABLE)
-      vis_table_kernel<T, C, true><<<p.num_sms * 8, kVisThreads, 0, s>>>(
-          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr,
-          table_view<T, C>(p), p.npad, p.counters + k, p.counters + p.K,
-          queue_batch(nk, p.num_sms * 8 * (kVisThreads / 32)));
-    else
-      vis_kernel<T, C, true><<<vis_blocks, kVisThreads, smem, s>>>(
-          static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, nullptr, grid, y, nullptr,
-          q, p.counters + k, p.counters + p.K, queue_batch(nk, vis_blocks * (kVisThreads / 32)));
-    PHI_CUDA_TRY(cudaGetLastError());
+    PHI_TRY_ST((launch_group_kernel<T, C, true>(p, g, nullptr, grids, y, nullptr, s)));
     timer_end(p, ev, PHI_STAGE_GRID, s);
     ev = timer_begin(p, s);
-    if (cufftSetStream(p.fft, s) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
-    cufftResult fr;
-    if (sizeof(T) == 8)
-      fr = cufftExecZ2Z(p.fft, reinterpret_cast<cufftDoubleComplex*>(grid),
-                        reinterpret_cast<cufftDoubleComplex*>(grid), CUFFT_INVERSE);
-    else
-      fr = cufftExecC2C(p.fft, reinterpret_cast<cufftComplex*>(grid),
-                        reinterpret_cast<cufftComplex*>(grid), CUFFT_INVERSE);
-    if (fr != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    PHI_TRY_ST((fft_group<T, C>(p, grids, n, CUFFT_INVERSE, s)));
     timer_end(p, ev, PHI_STAGE_FFT, s);
     ev = timer_begin(p, s);
-    finish_kernel<T, C><<<img_blocks, 256, 0, s>>>(grid, p.omn_pix,
-                                                   static_cast<const T*>(p.corr_pix), p.N, p.npad,
-                                                   p.wbar[k], x, first ? 0 : 1);
+    finish_kernel<T, C><<<p.num_sms * 4, 256, 0, s>>>(
+        grids, p.omn_pix, static_cast<const T*>(p.corr_pix), p.N, p.npad, p.wbar_dev,
+        p.group_stacks_dev + p.group_off[g], n, x, g == 0 ? 0 : 1);
     PHI_CUDA_TRY(cudaGetLastError());
     timer_end(p, ev, PHI_STAGE_FINISH, s);
-    first = false;
   }
-  if (first) PHI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)p.N * p.N, s));
+  if (ngroups == 0) PHI_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(T) * (size_t)p.N * p.N, s));
   return PHI_OK;
 }
 

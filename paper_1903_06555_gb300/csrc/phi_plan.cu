@@ -223,7 +223,9 @@ __global__ void records_kernel(const double* __restrict__ uvw, const uint8_t* __
     r.bv = static_cast<int32_t>(bv);
     r.dw = dw;
     r.weight = static_cast<T>(weights ? weights[o] : 1.0);
-    r.jw = per_vis ? J + 2 * static_cast<int32_t>(ceil(fabs(dw) * c_support)) : stack_jw[s];
+    r.jw = static_cast<decltype(r.jw)>(per_vis ? J + 2 * static_cast<int32_t>(ceil(fabs(dw) * c_support))
+                                               : stack_jw[s]);
+    r.stack = static_cast<decltype(r.stack)>(s);
     recs[i] = r;
     perm[i] = o | (flag[o] ? 0x80000000u : 0u);
   }
@@ -285,6 +287,10 @@ void free_plan(Plan* p) {
   cudaFree(p->table);
   cudaFree(p->item_start);
   cudaFree(p->item_key);
+  cudaFree(p->group_stacks_dev);
+  cudaFree(p->stack_slot_dev);
+  cudaFree(p->wbar_dev);
+  if (p->fft_batch_ok) cufftDestroy(p->fft_batch);
 }
 
 template <typename X>
@@ -325,6 +331,7 @@ int validate(const phi_plan_desc& d, int64_t M) {
   if (d.kb_beta < 0.0 || d.cycles_per_panel < 0.0) return PHI_ERR_ARG;
   if (d.kernel_mode != PHI_KERNEL_QUADRATURE && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
   if (d.grid_staging != 0 && d.grid_staging != 1) return PHI_ERR_ARG;
+  if (d.max_grid_mib < 0 || d.reserved0 != 0) return PHI_ERR_ARG;
   if (d.grid_staging && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
   if (d.kernel_mode == PHI_KERNEL_TABLE && !(d.table_tol > 0.0 && d.table_tol < 1.0))
     return PHI_ERR_ARG;
@@ -635,8 +642,32 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   PHI_CUDA_TRY(owned_alloc(p, &p.omn_pix, static_cast<size_t>(p.N) * p.N));
   PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.corr_pix),
                            tsize * p.N * static_cast<size_t>(p.N)));
+  // Stack groups: the stacks with visibilities, `group` at a time, their
+  // grids resident together (as many as fit max_grid_mib, at least one).
+  const size_t grid_bytes = 2 * tsize * static_cast<size_t>(p.npad) * p.npad;
+  p.group_stacks.clear();
+  for (int q = 0; q < K; ++q)
+    if (p.stack_off[q + 1] > p.stack_off[q]) p.group_stacks.push_back(q);
+  const double budget = (d.max_grid_mib > 0 ? d.max_grid_mib : 4096) * 1048576.0;
+  p.group = static_cast<int>(std::max<double>(1.0, std::floor(budget / grid_bytes)));
+  p.group = std::max(1, std::min<int>(p.group, static_cast<int>(p.group_stacks.size())));
+  p.group_off.assign(1, 0);
+  for (size_t g = 0; g < p.group_stacks.size(); g += p.group)
+    p.group_off.push_back(static_cast<int64_t>(std::min(p.group_stacks.size(), g + p.group)));
+  std::vector<int32_t> slot(K, 0);
+  for (size_t g = 0; g + 1 < p.group_off.size(); ++g)
+    for (int64_t i = p.group_off[g]; i < p.group_off[g + 1]; ++i)
+      slot[p.group_stacks[i]] = static_cast<int32_t>(i - p.group_off[g]);
+  PHI_CUDA_TRY(owned_alloc(p, &p.group_stacks_dev, std::max<size_t>(1, p.group_stacks.size())));
+  PHI_CUDA_TRY(owned_alloc(p, &p.stack_slot_dev, K));
+  PHI_CUDA_TRY(owned_alloc(p, &p.wbar_dev, K));
+  if (!p.group_stacks.empty())
+    PHI_CUDA_TRY(cudaMemcpyAsync(p.group_stacks_dev, p.group_stacks.data(),
+                                 4 * p.group_stacks.size(), cudaMemcpyHostToDevice, s));
+  PHI_CUDA_TRY(cudaMemcpyAsync(p.stack_slot_dev, slot.data(), 4 * K, cudaMemcpyHostToDevice, s));
+  PHI_CUDA_TRY(cudaMemcpyAsync(p.wbar_dev, p.wbar.data(), 8 * K, cudaMemcpyHostToDevice, s));
   PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.grid),
-                           2 * tsize * static_cast<size_t>(p.npad) * p.npad));
+                           grid_bytes * static_cast<size_t>(p.group)));
   PHI_TRY(launch_node_tables(p, s));
   PHI_TRY(launch_pixel_tables(p, s));
   if (d.kernel_mode == PHI_KERNEL_TABLE) {
@@ -662,6 +693,17 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   if (cufftMakePlan2d(p.fft, p.npad, p.npad, f64 ? CUFFT_Z2Z : CUFFT_C2C, &work) != CUFFT_SUCCESS)
     return PHI_ERR_OOM;
   p.device_bytes += static_cast<int64_t>(work);
+  if (p.group > 1) {
+    if (cufftCreate(&p.fft_batch) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
+    p.fft_batch_ok = true;
+    int dims[2] = {p.npad, p.npad};
+    const int dist = p.npad * p.npad;
+    size_t work_b = 0;
+    if (cufftMakePlanMany(p.fft_batch, 2, dims, nullptr, 1, dist, nullptr, 1, dist,
+                          f64 ? CUFFT_Z2Z : CUFFT_C2C, p.group, &work_b) != CUFFT_SUCCESS)
+      return PHI_ERR_OOM;
+    p.device_bytes += static_cast<int64_t>(work_b);
+  }
   PHI_CUDA_TRY(cudaStreamSynchronize(s));
   return PHI_OK;
 }
@@ -770,7 +812,7 @@ extern "C" int phi_plan_info(phi_plan_t plan, phi_plan_summary* info, double* wb
     info->window_radius = p.R;
     info->support_coeff = p.c_support;
     info->kernel_mode = p.d.kernel_mode;
-    info->reserved0 = 0;
+    info->group = p.group;
     info->table_n_rho = p.table_nr;
     info->table_n_w = p.table_nw;
     info->table_h_rho = p.table_hr;

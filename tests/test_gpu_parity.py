@@ -239,3 +239,26 @@ def test_mwa_snapshot_adjoint_at_full_size(mwa):
     lhs = torch.real(torch.vdot(y.to(torch.complex128), plan.degrid(x).to(torch.complex128))).item()
     rhs = torch.sum(x.double() * plan.grid(y).double()).item()
     assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+@pytest.mark.parametrize("mode", ["quadrature", "table"])
+def test_stack_groups_match_one_grid_at_a_time(mode):
+    """Grids of several stacks resident together (batched FFTs, one fused
+    launch per group) give the same operator as one stack at a time: groups
+    of 2 over 5 stacks (the last group takes the single-transform path)."""
+    geo = oracle_geo(128)
+    uvw = W.uvw_disk(2000, 60.0, 40.0, 61)
+    x = torch.from_numpy(W.point_sources(128, 20, 61)).cuda().float()
+    yr = torch.from_numpy(W.random_vis(2000, 62)).cuda().to(torch.complex64)
+    out = {}
+    for mib in (1, 0):          # 1 MiB: two 256^2 grids per group; 0: all five together
+        plan = gpu_plan(uvw, geo, 5, True, kernel_mode=mode, max_grid_mib=mib)
+        info = plan.info()
+        out[mib] = (info["group"], plan.degrid(x), plan.grid(yr))
+    assert out[1][0] == 2 and out[0][0] == 5
+    assert torch.equal(out[1][1], out[0][1])
+    d1, d0 = out[1][2], out[0][2]
+    assert (torch.linalg.vector_norm(d1 - d0) / torch.linalg.vector_norm(d0)).item() < 1e-6
+    if mode == "quadrature":
+        op = O.make_plan(uvw, geo, 5, True)
+        assert O.rel_l2(out[1][1].cpu().numpy(), O.degrid(op, x.double().cpu().numpy())) < TOL32
