@@ -262,3 +262,34 @@ def test_stack_groups_match_one_grid_at_a_time(mode):
     if mode == "quadrature":
         op = O.make_plan(uvw, geo, 5, True)
         assert O.rel_l2(out[1][1].cpu().numpy(), O.degrid(op, x.double().cpu().numpy())) < TOL32
+
+
+GEOMETRIES = {
+    # name: (N, os, fov_deg, J, alpha, n_vis, K, fold)
+    "os1.5-J6": (96, 1.5, 10.0, 6, 1.0, 600, 2, True),
+    "J8-alpha1.5": (128, 2.0, 20.0, 8, 1.5, 500, 3, False),
+    "K126-many-empty": (64, 2.0, 20.0, 4, 1.0, 400, 126, True),
+}
+
+
+@pytest.mark.parametrize("name", list(GEOMETRIES))
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_geometry_variants_match_oracle(name, precision):
+    N, os_, fov, J, alpha, m, k, fold = GEOMETRIES[name]
+    geo = O.Geometry(N, os_, math.radians(fov), float(J), alpha=alpha, tol_rel=1e-13,
+                     tol_abs=1e-13)
+    radius = 0.45 * geo.Npad * geo.du / 2
+    uvw = W.uvw_disk(m, radius, 30.0, 71)
+    x = W.point_sources(N, 10, 71)
+    yr = W.random_vis(m, 72)
+    op = O.make_plan(uvw, geo, k, fold)
+    plan = gpu_plan(uvw, geo, k, fold, precision)
+    rd = torch.float64 if precision == "f64" else torch.float32
+    cd = torch.complex128 if precision == "f64" else torch.complex64
+    tol = TOL64 if precision == "f64" else TOL32
+    y = plan.degrid(to_t(x, rd)).cpu().numpy()
+    assert O.rel_l2(y, O.degrid(op, x)) < tol
+    d = plan.grid(to_t(yr, cd)).cpu().numpy()
+    assert O.rel_l2(d, O.grid(op, yr)) < tol
+    info = plan.info()
+    assert info["npad"] == geo.Npad and info["kmeans_sweeps"] == op.sweeps
