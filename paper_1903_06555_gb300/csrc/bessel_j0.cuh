@@ -4,20 +4,18 @@
 // Method: Abramowitz & Stegun (1964), 9.4.1 for pi u <= 3 (polynomial in
 // (x/3)^2, |error| < 5e-8) and 9.4.3 for pi u >= 3 (J0 = x^{-1/2} f0 cos theta0
 // with f0 and theta0 polynomials in 3/x, |error| < 1.6e-8 and 7e-8 rad).
-// The phase is carried in half-cycles, phi' = theta0/pi + 1/4 = u +
-// (theta0 - x + pi/4)/pi, reduced exactly by its nearest integer n, so the
-// cosine only ever sees an argument in [-3pi/4, pi/4]:
-// cos(theta0) = (-1)^n cos(pi (phi' - n) - pi/4).  The whole evaluation costs
-// a reciprocal square root, a short-range cosine and ~20 FMA-pipe operations.
+// The phase theta0 = pi (u + sum_k b_k t^k / pi) - pi/4 is formed in FP32 and
+// handed to the hardware cosine, which reduces it by whole turns itself.  The
+// argument's own FP32 rounding (relative 6e-8, i.e. 6e-6 rad at 100 rad, the
+// largest phase a 64-tap support reaches) dominates that reduction's error, so
+// an explicit reduction in half-cycles buys no accuracy; dropping it saves ~5
+// of ~30 instructions per evaluation.  The whole evaluation costs a
+// reciprocal square root, a cosine and ~20 FMA-pipe operations.
 // Polynomials in s = 1/u absorb the factors (3/pi)^k, 1/pi and 1/sqrt(pi).
 #pragma once
 
 #ifndef PHI_HD
 #define PHI_HD __host__ __device__
-#endif
-
-#if !defined(__CUDA_ARCH__)
-#include <cstring>
 #endif
 
 namespace phi {
@@ -38,33 +36,13 @@ PHI_HD inline float j0_rsqrt(float x) {
 #endif
 }
 
-// cos on |a| <= pi: the hardware approximation on the device (absolute
-// error ~5e-7 on this range), the libm cosine on the host.
+// cos: the hardware approximation on the device (absolute error ~5e-7 on
+// [-pi, pi], growing with |a| like the FP32 rounding of a), libm on the host.
 PHI_HD inline float j0_cos(float a) {
 #if defined(__CUDA_ARCH__)
   return __cosf(a);
 #else
   return cosf(a);
-#endif
-}
-
-PHI_HD inline int j0_float_bits(float x) {
-#if defined(__CUDA_ARCH__)
-  return __float_as_int(x);
-#else
-  int b;
-  memcpy(&b, &x, sizeof(b));
-  return b;
-#endif
-}
-
-PHI_HD inline float j0_bits_float(int b) {
-#if defined(__CUDA_ARCH__)
-  return __int_as_float(b);
-#else
-  float x;
-  memcpy(&x, &b, sizeof(x));
-  return x;
 #endif
 }
 
@@ -103,17 +81,9 @@ PHI_HD inline float j0_halfcycles(float u) {
   d = j0_fma(d, s, 0.00262573f * c3 * ip);
   d = j0_fma(d, s, -0.00003954f * c2 * ip);
   d = j0_fma(d, s, -0.04166397f * c1 * ip);
-  // phi' = theta0/pi + 1/4 = u + sum_k b_k t^k / pi
+  // theta0 = pi (u + sum_k b_k t^k / pi) - pi/4, reduced by the cosine itself
   const float phi = j0_fma(d, s, u);
-  // Round phi' to the nearest integer n with the 1.5 * 2^23 shift (exact for
-  // |phi'| < 2^22); the low mantissa bit of the shifted value is n's parity.
-  const float big = 12582912.0f;
-  const float shifted = phi + big;
-  const float n = shifted - big;
-  // cos(theta0) = (-1)^n cos(pi (phi' - n) - pi/4), argument in [-3pi/4, pi/4]
-  const float arg = j0_fma(phi - n, 3.14159265358979f, -0.785398163397448f);
-  const float v = (r * f0) * j0_cos(arg);
-  return j0_bits_float(j0_float_bits(v) ^ (j0_float_bits(shifted) << 31));
+  return (r * f0) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
 }
 
 }  // namespace phi

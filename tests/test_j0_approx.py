@@ -1,5 +1,5 @@
-"""The device FP32 J0 (csrc/bessel_j0.cuh, Abramowitz & Stegun 9.4.1/9.4.3
-with a half-cycle cosine) compiled for the host and checked against scipy."""
+"""The device FP32 J0 (csrc/bessel_j0.cuh, Abramowitz & Stegun 9.4.1/9.4.3)
+compiled for the host and checked against scipy."""
 import os
 import subprocess
 
@@ -53,4 +53,8 @@ def test_j0_halfcycles_against_scipy():
     ulp = np.spacing(np.maximum(u, 1.0).astype(np.float32)).astype(np.float64)
     big = np.pi * u > 3
     assert np.all(err[big] <= 2e-7 + 2 * env[big] * np.pi * ulp[big])
-    assert np.sqrt(np.mean(err ** 2)) < 1.5e-7
+    # rms: the formula's 1e-7 and the rounding of u (to ulp(u)/2, scaled by
+    # pi) and of the phase theta0 (to ulp(theta0)/2), each uniform
+    th = np.spacing(np.maximum(np.pi * u, 1.0).astype(np.float32)).astype(np.float64)
+    rounding = env * np.sqrt((np.pi * ulp) ** 2 + th ** 2) / np.sqrt(24.0)
+    assert np.sqrt(np.mean(err ** 2)) < 1.25 * np.hypot(1e-7, np.sqrt(np.mean(rounding ** 2)))
