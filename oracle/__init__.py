@@ -227,6 +227,8 @@ class Geometry:
         self.Npad = int(round(self.os * self.N))
         if self.Npad % 2 or self.N % 2:
             raise ValueError("N and os*N must be even")
+        if self.J != int(self.J) or int(self.J) % 2 or self.J < 2:
+            raise ValueError("support J must be an even integer >= 2")
         if self.beta == 0.0:
             self.beta = beatty_beta(self.J, self.os)
         self.dl = self.fov / self.N

@@ -277,6 +277,15 @@ void orc_direct(const double* xv, const double* lp, const double* mp, int64_t np
   }
 }
 
+// First tap of a J-wide box: q0 = floor(u - J/2) + 1, the smallest grid
+// index above u - J/2 (the J nearest grid points, box half-open on the low
+// side).  J is even, so q0 = floor(u) - J/2 + 1 exactly; forming u - J/2 in
+// floating point first could round across an integer (u = -28 - 3.6e-15 with
+// J = 8 gives -32 exactly) and shift the box by one.
+static int64_t first_tap(double u, int J) {
+  return static_cast<int64_t>(std::floor(u)) - J / 2 + 1;
+}
+
 // Degridding for one w-stack (Eq. GC_k):
 //   y_i = W_i sum_{taps} [GC](|(u_i, v_i)/du - q|, dw_i) Xhat[q mod Npad],
 // taps q = q0 + (a, b), a, b in [0, Jw_i), q0 = floor(u_i/du - Jw_i/2) + 1;
@@ -294,8 +303,8 @@ void orc_degrid(const double* grid, int64_t npad, const double* prm, const doubl
     cd acc(0.0, 0.0);
     int J = jw[i];
     if (J > 0) {
-      int64_t q0u = static_cast<int64_t>(std::floor(upix[i] - 0.5 * J)) + 1;
-      int64_t q0v = static_cast<int64_t>(std::floor(vpix[i] - 0.5 * J)) + 1;
+      int64_t q0u = first_tap(upix[i], J);
+      int64_t q0v = first_tap(vpix[i], J);
       for (int b = 0; b < J; ++b) {
         for (int a = 0; a < J; ++a) {
           double du_ = upix[i] - static_cast<double>(q0u + a);
@@ -339,8 +348,8 @@ void orc_grid(double* grid, int64_t npad, const double* prm, const double* rule,
     for (int64_t i = c0; i < c1; ++i) {
       int J = jw[i];
       if (J <= 0) continue;
-      int64_t q0u = static_cast<int64_t>(std::floor(upix[i] - 0.5 * J)) + 1;
-      int64_t q0v = static_cast<int64_t>(std::floor(vpix[i] - 0.5 * J)) + 1;
+      int64_t q0u = first_tap(upix[i], J);
+      int64_t q0v = first_tap(vpix[i], J);
       cd* kk = &kbuf[static_cast<size_t>(i - c0) * jmax * jmax];
       for (int b = 0; b < J; ++b)
         for (int a = 0; a < J; ++a) {
@@ -356,8 +365,8 @@ void orc_grid(double* grid, int64_t npad, const double* prm, const double* rule,
     for (int64_t i = c0; i < c1; ++i) {
       int J = jw[i];
       if (J <= 0) continue;
-      int64_t q0u = static_cast<int64_t>(std::floor(upix[i] - 0.5 * J)) + 1;
-      int64_t q0v = static_cast<int64_t>(std::floor(vpix[i] - 0.5 * J)) + 1;
+      int64_t q0u = first_tap(upix[i], J);
+      int64_t q0v = first_tap(vpix[i], J);
       cd yt(y[2 * i], y[2 * i + 1]);
       if (flag[i]) yt = std::conj(yt);
       yt *= weight[i];
@@ -417,8 +426,8 @@ void orc_degrid_table(const double* grid, int64_t npad, const double* tab, int64
     cd acc(0.0, 0.0);
     int J = jw[i];
     if (J > 0) {
-      int64_t q0u = static_cast<int64_t>(std::floor(upix[i] - 0.5 * J)) + 1;
-      int64_t q0v = static_cast<int64_t>(std::floor(vpix[i] - 0.5 * J)) + 1;
+      int64_t q0u = first_tap(upix[i], J);
+      int64_t q0v = first_tap(vpix[i], J);
       for (int b = 0; b < J; ++b)
         for (int a = 0; a < J; ++a) {
           double du_ = upix[i] - static_cast<double>(q0u + a);
@@ -442,8 +451,8 @@ void orc_grid_table(double* grid, int64_t npad, const double* tab, int64_t nr, i
   for (int64_t i = 0; i < nvis; ++i) {
     int J = jw[i];
     if (J <= 0) continue;
-    int64_t q0u = static_cast<int64_t>(std::floor(upix[i] - 0.5 * J)) + 1;
-    int64_t q0v = static_cast<int64_t>(std::floor(vpix[i] - 0.5 * J)) + 1;
+    int64_t q0u = first_tap(upix[i], J);
+    int64_t q0v = first_tap(vpix[i], J);
     cd yt(y[2 * i], y[2 * i + 1]);
     if (flag[i]) yt = std::conj(yt);
     yt *= weight[i];

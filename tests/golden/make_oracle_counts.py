@@ -37,8 +37,8 @@ def main(per_stack=60):
         evals = []
         for i in sel:
             J = int(plan.jw[i])
-            q0u = np.floor(plan.upix[i] - J / 2) + 1
-            q0v = np.floor(plan.vpix[i] - J / 2) + 1
+            q0u = np.floor(plan.upix[i]) - J // 2 + 1      # floor(u - J/2) + 1, exact for even J
+            q0v = np.floor(plan.vpix[i]) - J // 2 + 1
             a = np.arange(J)
             du_ = plan.upix[i] - (q0u + a)
             dv_ = plan.vpix[i] - (q0v + a)

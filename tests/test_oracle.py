@@ -383,6 +383,31 @@ def test_visibilities_outside_grid_are_dropped():
     assert y[0] == 0 and y[1] == 0 and y[2] != 0
 
 
+@pytest.mark.parametrize("J", [4, 8])
+def test_tap_box_is_exact_for_positions_one_ulp_from_integers(J):
+    """The J x J box holds the J nearest grid points per axis, q in
+    (u - J/2, u + J/2] (Sec. 2; half-open on the low side).  Pin: the
+    footprint of one gridded visibility against that box computed in exact
+    rational arithmetic, at doubles one ulp either side of integers and
+    half-integers, where forming u - J/2 in floating point would round."""
+    from fractions import Fraction
+    geo = O.Geometry(128, 2.0, math.radians(20.0), float(J), tol_rel=1e-8, tol_abs=1e-8)
+    plan = O.make_plan(np.array([[0.0, 0.0, 3.0]]), geo, 1, False)
+    vals = []
+    for k in (-28.0, -3.0, 0.0, 5.0, 17.5, -9.5):
+        vals += [np.nextafter(k, -np.inf), k, np.nextafter(k, np.inf)]
+    for u in vals:
+        v = vals[(vals.index(u) + 4) % len(vals)]
+        plan.upix[0], plan.vpix[0] = u, v
+        grids, _, _ = O.grid_to_stacks(plan, np.array([1.0 + 0.0j]))
+        g = grids[0]
+        rows, cols = np.nonzero(np.abs(g) > 0)
+        for pos, found in ((u, set(cols.tolist())), (v, set(rows.tolist()))):
+            q0 = math.floor(Fraction(float(pos)) - Fraction(J, 2)) + 1
+            want = {q % geo.Npad for q in range(q0, q0 + J)}
+            assert found == want, (float(pos).hex(), J)
+
+
 # ---------------------------------------------------------------- pre-sampled w-planes
 
 @pytest.fixture(scope="module")
