@@ -182,7 +182,7 @@ def measured_peaks():
 def kernel_source_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("phi_ops.cu", "bessel_j0.cuh", "phi_internal.cuh"):
+    for f in ("phi_ops.cu", "bessel_j0.cuh", "phi_internal.cuh", "table_index.cuh"):
         with open(os.path.join(ROOT, "paper_1903_06555_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -24,6 +24,7 @@
 #include <mutex>
 
 #include "bessel_j0.cuh"
+#include "table_index.cuh"
 #include "phi_internal.cuh"
 
 namespace phi {
@@ -492,26 +493,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
 // ---------------------------------------------------------------------------
 // Pre-sampled 1-D w-planes (Sec. 5.1.1)
 // ---------------------------------------------------------------------------
-
-// Table position of a scaled radius s >= 0: ir = floor(s) clamped to
-// last, fr = s - ir.  FP32 uses the 2^23 shift so no conversion instruction
-// is needed (an exact integer s may come out as ir = s - 1, fr = 1: the
-// same interpolated value).
-__device__ __forceinline__ void table_index(float s, int last, float last_f, int& ir, float& fr) {
-  const float big = 8388608.0f;                       // 2^23
-  const float t = (s - 0.5f) + big;                   // low bits: nearest integer to s - 1/2
-  ir = __float_as_int(t) - __float_as_int(big);
-  fr = s - (t - big);
-  if (!(s < last_f)) {                                // beyond the table (or NaN)
-    ir = last;
-    fr = s - last_f;
-  }
-}
-__device__ __forceinline__ void table_index(double s, int last, double last_f, int& ir,
-                                            double& fr) {
-  ir = s < last_f ? static_cast<int>(s) : last;
-  fr = s - static_cast<double>(ir);
-}
 
 // Two adjacent w-planes at one radius: {K(j, i), K(j + 1, i)}.
 template <typename C> struct __align__(2 * sizeof(C)) KPair { C a, b; };

@@ -73,3 +73,54 @@ def test_table_adjoint_and_closeness_to_quadrature(case):
     yq = quad.degrid(xs)
     yt = plan.degrid(xs)
     assert (torch.linalg.vector_norm(yt - yq) / torch.linalg.vector_norm(yq)).item() < 2e-3
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_table_on_grid_points_matches_oracle(precision):
+    """Visibilities exactly on grid points (and a hair off them): their
+    central taps sit at table position s ~ 0, the first interval's left end."""
+    geo = O.Geometry(128, 2.0, math.radians(20.0), 4.0, tol_rel=1e-13, tol_abs=1e-13)
+    uvw = W.uvw_disk(600, 60.0, 40.0, 71)
+    k = np.round(uvw[:300, :2] / geo.du)
+    uvw[:200, :2] = k[:200] * geo.du
+    uvw[200:300, :2] = (k[200:300] + 1e-4) * geo.du
+    op = O.make_plan(uvw, geo, 3, True)
+    tab = O.make_table(op, TABLE_TOL)
+    x = W.point_sources(128, 20, 72)
+    yr = W.random_vis(len(uvw), 73)
+    tol = 1e-12 if precision == "f64" else 1e-6
+    plan = phi.Plan(torch.from_numpy(uvw), image_n=128, fov_rad=geo.fov, n_stacks=3,
+                    conj_fold=1, precision=precision, quad_rel_tol=tol, quad_abs_tol=tol,
+                    kernel_mode="table", table_tol=TABLE_TOL)
+    rd = torch.float64 if precision == "f64" else torch.float32
+    cd = torch.complex128 if precision == "f64" else torch.complex64
+    ptol = 1e-10 if precision == "f64" else 1e-5
+    y = plan.degrid(torch.from_numpy(x).to("cuda", rd)).cpu().numpy()
+    y_ref = O.degrid_table(op, x, tab)
+    assert O.rel_l2(y, y_ref) < ptol
+    assert O.rel_l2(y[:300], y_ref[:300]) < ptol
+    xg = plan.grid(torch.from_numpy(yr).to("cuda", cd)).cpu().numpy()
+    assert O.rel_l2(xg, O.grid_table(op, yr, tab)) < ptol
+
+
+def test_table_close_to_quadrature_at_full_size():
+    """The bench workload (2048^2 image, 1.95M visibilities, 8 stacks, fold on)
+    at table_tol 1e-4: bilinear interpolation bounds each kernel sample's
+    error by table_tol times the kernel's scale, so the visibilities differ
+    from the quadrature path by less than table_tol, in L2 and per
+    visibility relative to the largest."""
+    wl = W.mwa_snapshot()
+    uvw = torch.from_numpy(W.uvw_for(wl))
+    geo = O.geometry_from(wl)
+    common = dict(image_n=wl.image_n, fov_rad=geo.fov, n_stacks=wl.n_stacks,
+                  conj_fold=int(wl.conj_fold))
+    x = torch.from_numpy(W.point_sources(wl.image_n, wl.n_sources, wl.seed)).cuda().float()
+    ys = {}
+    for mode in ("quadrature", "table"):
+        p = phi.Plan(uvw, kernel_mode=mode, table_tol=1e-4, **common)
+        ys[mode] = p.degrid(x).to(torch.complex128)
+        p.close()
+    d = ys["table"] - ys["quadrature"]
+    scale = torch.abs(ys["quadrature"]).max()
+    assert (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(ys["quadrature"])).item() < 1e-4
+    assert (torch.abs(d).max() / scale).item() < 1e-4
