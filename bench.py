@@ -212,6 +212,40 @@ def load_oracle_counts():
         return json.load(f)
 
 
+def covered_grid_cells(uvw_np, info, conj_fold):
+    """Distinct grid cells that the J_w x J_w boxes of the kept visibilities
+    cover, summed over the stacks: the grid part of a launch's minimum HBM
+    traffic (each such cell is read, or written, at least once).  Host-side
+    from the plan's own centres and supports: fold to w >= 0, nearest centre
+    (first on ties), drop outside [-Npad/2, Npad/2), box from
+    floor(u/du) - J_w/2 + 1, circular."""
+    import scipy.ndimage as nd
+    u, v, w = (np.array(uvw_np[:, i], np.float64) for i in range(3))
+    if conj_fold:
+        f = w < 0
+        u[f], v[f], w[f] = -u[f], -v[f], -w[f]
+    npad, du = int(info["npad"]), float(info["du"])
+    wbar = np.asarray(info["wbar"], np.float64)
+    jw = np.asarray(info["jw"], np.int64)
+    stack = np.argmin(np.abs(w[:, None] - wbar[None, :]), axis=1)
+    up, vp = u / du, v / du
+    keep = (up >= -npad / 2) & (up < npad / 2) & (vp >= -npad / 2) & (vp < npad / 2)
+    total = 0
+    for k in range(len(wbar)):
+        sel = keep & (stack == k)
+        if not sel.any():
+            continue
+        J = int(jw[k])
+        q0u = (np.floor(up[sel]).astype(np.int64) - J // 2 + 1) % npad
+        q0v = (np.floor(vp[sel]).astype(np.int64) - J // 2 + 1) % npad
+        m = np.zeros((npad, npad), np.uint8)
+        m[q0v, q0u] = 1
+        for ax in (0, 1):
+            m = nd.maximum_filter1d(m, size=J, axis=ax, mode="wrap", origin=(J - 1) // 2)
+        total += int(np.count_nonzero(m))
+    return total
+
+
 def flush_l2(buf):
     buf.add_(1.0)   # 256 MiB read-modify-write: larger than the 129 MB L2
 
@@ -385,22 +419,25 @@ def run_ours(args, ws, rank, local):
     peak_fp32 = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     clocks = clk.summary()
     if args.kernel_mode == "table":
-        # HBM bytes a launch must move at least: records + permutation +
-        # visibilities of its stack, its grid once, the plane pairs once
-        jw = np.array(info["jw"], float)
+        # HBM bytes one launch (all stacks of the resident group) must move at
+        # least: records + permutation + visibility per visibility, the
+        # covered grid cells once, the plane pairs once
         cnt = np.array(info["counts"], float)
-        grid_b = 8.0 * info["npad"] ** 2
+        cells = covered_grid_cells(uvw_np, info, desc.get("conj_fold", 0))
         table_b = 16.0 * info["table_n_rho"] * (info["table_n_w"] - 1)
-        bytes_step = float((cnt * (32 + 4 + 8)).sum()) + (cnt > 0).sum() * (grid_b + table_b)
+        groups = max(1, int(round(launches_per_step)))
+        bytes_step = float(cnt.sum()) * (32 + 4 + 8) + 8.0 * cells + groups * table_b
         ach_gbs = bytes_step / launches_per_step / ((ms_dom / n_dom) / 1e3) / 1e9
         hbm = peaks.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "kernel": f"vis_table_kernel ({dom})", "achieved": ach_gbs,
                 "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
                 "traffic": profiled_traffic("table_" + dom),
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "work_note": "records 36 B + visibility 8 B per visibility, the stack's grid "
-                             "and the plane pairs once per launch; the kernel is L1/TEX bound "
-                             "(92% of that pipe in ncu), far below the HBM roofline"}
+                "covered_grid_cells": cells,
+                "work_note": "records 32 B + permutation 4 B + visibility 8 B per visibility, "
+                             "8 B per grid cell covered by a kernel box, the plane pairs once "
+                             "per launch; the kernel is L1/TEX bound (92% of that pipe in ncu), "
+                             "far below the HBM roofline"}
     else:
         roof = {"bound": "alu", "kernel": f"vis_kernel ({dom})", "achieved": achieved,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,

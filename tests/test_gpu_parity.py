@@ -201,6 +201,31 @@ def test_max_support_exceeded_is_an_error():
     assert e.value.status == phi.PHI_ERR_SUPPORT
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_visibilities_on_grid_points_match_oracle(precision):
+    """Visibilities on grid points and one ulp either side of them (u/du an
+    integer, or the double next to it): the J_w-wide box is the J_w nearest
+    grid points, half-open on its low side (Sec. 2), decided on the exact
+    double u/du by both sides."""
+    geo = oracle_geo(128)
+    uvw = W.uvw_disk(500, 60.0, 40.0, 81)
+    k = np.round(uvw[:300, :2] / geo.du)
+    uvw[:100, :2] = k[:100] * geo.du
+    uvw[100:200, :2] = np.nextafter(k[100:200], -np.inf) * geo.du
+    uvw[200:300, :2] = np.nextafter(k[200:300], np.inf) * geo.du
+    op = O.make_plan(uvw, geo, 3, True)
+    x = W.point_sources(128, 20, 82)
+    yr = W.random_vis(len(uvw), 83)
+    plan = gpu_plan(uvw, geo, 3, True, precision)
+    rd, cd = (torch.float64, torch.complex128) if precision == "f64" else (torch.float32, torch.complex64)
+    tol = TOL64 if precision == "f64" else TOL32
+    y = plan.degrid(to_t(x, rd)).cpu().numpy()
+    y_ref = O.degrid(op, x)
+    assert O.rel_l2(y, y_ref) < tol
+    assert O.rel_l2(y[:300], y_ref[:300]) < tol
+    assert O.rel_l2(plan.grid(to_t(yr, cd)).cpu().numpy(), O.grid(op, yr)) < tol
+
+
 # ----------------------------------------------------------------------------- full size
 
 @pytest.fixture(scope="module")
