@@ -52,6 +52,8 @@ def parse():
                     help="mwa: the headline operator benchmark; serve: the serving stream; "
                          "plan: Algorithm 1 and the fold at the paper's scale")
     ap.add_argument("--serve-requests", type=int, default=200)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="offered load of the Poisson stream as a fraction of the measured capacity")
     ap.add_argument("--serve-full-scale", type=int, default=1,
                     help="append the 126.6M-visibility request to the serving stream")
     ap.add_argument("--support-rule", default="stack", choices=["stack", "vis"])
@@ -561,7 +563,7 @@ def poisson_arrivals(reqs, rate, seed=0):
 def run_serve(args):
     """The serving workload: a closed-loop pass over requests drawn from the
     stream's distribution measures capacity (kept visibilities/s); the
-    Poisson stream then arrives at 80% of it.  Requests whose support would
+    Poisson stream then arrives at `--serve-load` (default 80%) of it.  Requests whose support would
     exceed the cap are retried by the engine with twice the stacks."""
     from paper_1903_06555_gb300 import serve as S
     budget = 150 * 10 ** 9
@@ -574,8 +576,12 @@ def run_serve(args):
     reqs = serve_requests(args.serve_requests, seed=1)
     for r in reqs:
         r.raise_stacks = True
-    mean_kept = cap["vis"] / max(cap["ok"], 1)
-    rate = 0.8 * cap["vis_per_s"] / mean_kept
+    # offered load = arrival rate x mean kept visibilities per request of
+    # THIS stream (sizes are heavy-tailed: a small probe's own mean is far
+    # off) / the probe's throughput
+    kept_frac = cap["vis"] / max(cap["vis_submitted"], 1)
+    mean_kept = kept_frac * float(np.mean([r.uvw.shape[0] for r in reqs]))
+    rate = args.serve_load * cap["vis_per_s"] / mean_kept
     poisson_arrivals(reqs, rate)
     if args.serve_full_scale:
         from paper_1903_06555_gb300.serve import Request
@@ -608,7 +614,8 @@ def run_serve(args):
             "workload": "serving: Poisson stream of %d observations (5e4-2e7 vis, 512^2-8192^2, "
                         "|w|max 50-3000, K 1-64 raised to fit J_w <= 64) + 126.6M-vis 8192^2 request"
                         % args.serve_requests,
-            "capacity_closed_loop": cap, "arrival_rate_per_s": rate, "hbm_budget_bytes": budget,
+            "capacity_closed_loop": cap, "offered_load": args.serve_load,
+            "mean_kept_per_request": mean_kept, "arrival_rate_per_s": rate, "hbm_budget_bytes": budget,
             "peak_admitted_bytes": peak, "summary": summ, "stacks_raised": raised,
             "full_scale": None if not full_res else {
                 "status": full_res[0].status, "error": full_res[0].error,

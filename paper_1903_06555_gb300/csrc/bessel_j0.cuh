@@ -28,9 +28,14 @@ PHI_HD inline float j0_fma(float a, float b, float c) {
 #endif
 }
 
+// Device: the hardware approximations with subnormals flushed (PTX .ftz):
+// the asymptotic branch only sees u >= 0.95, so no subnormal input occurs,
+// and the flush spares the subnormal handling around the hardware op.
 PHI_HD inline float j0_rsqrt(float x) {
 #if defined(__CUDA_ARCH__)
-  return rsqrtf(x);
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 #else
   return 1.0f / sqrtf(x);
 #endif
@@ -40,7 +45,9 @@ PHI_HD inline float j0_rsqrt(float x) {
 // [-pi, pi], growing with |a| like the FP32 rounding of a), libm on the host.
 PHI_HD inline float j0_cos(float a) {
 #if defined(__CUDA_ARCH__)
-  return __cosf(a);
+  float y;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(a));
+  return y;
 #else
   return cosf(a);
 #endif

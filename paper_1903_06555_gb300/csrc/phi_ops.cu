@@ -94,6 +94,14 @@ __device__ __forceinline__ float j0_hc(float u) { return j0_halfcycles(u); }
 __device__ __forceinline__ double j0_hc(double u) { return j0(kPi * u); }
 __device__ __forceinline__ float gk_node_c(float, int j) { return c_gk_node_f[j]; }
 __device__ __forceinline__ double gk_node_c(double, int j) { return c_gk_node_d[j]; }
+// Square root for error estimates and tolerance tests only: the hardware
+// approximation in FP32 (relative error ~2^-22), the correctly rounded one in FP64.
+__device__ __forceinline__ float est_sqrt(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ double est_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ void sincos_pi(float a, float* s, float* c) { sincospif(a, s, c); }
 __device__ __forceinline__ void sincos_pi(double a, double* s, double* c) { sincospi(a, s, c); }
 
@@ -329,7 +337,7 @@ __device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np
       dr = fma(J, v.dr, dr);
       di = fma(J, v.di, di);
     }
-    err += sqrt(dr * dr + di * di);
+    err += est_sqrt(dr * dr + di * di);
   }
 }
 
@@ -365,7 +373,7 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
     }
     // err and |K| are both formed without cancellation (err from the
     // Kronrod-minus-Gauss weights), so the test runs in T.
-    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * sqrt(kr * kr + ki * ki));
+    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * est_sqrt(kr * kr + ki * ki));
     ok = (!active) || err <= lim;
     const bool any_bad = __any_sync(0xffffffffu, !ok);
     if (!any_bad || refine >= q.max_refine || 2 * npan > kMaxPanels) return cmake<C>(kr, ki);
@@ -1244,7 +1252,7 @@ __device__ C eval_chunk_capped(NodeVal<T>* sh, const QuadParams& q, T rho, bool 
       }
       built = 0;
     }
-    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * sqrt(kr * kr + ki * ki));
+    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * est_sqrt(kr * kr + ki * ki));
     ok = (!active) || err <= lim;
     const bool any_bad = __any_sync(0xffffffffu, !ok);
     if (!any_bad || refine >= q.max_refine || 2 * npan > max_panels) return cmake<C>(kr, ki);
