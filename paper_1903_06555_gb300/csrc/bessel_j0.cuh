@@ -53,18 +53,24 @@ PHI_HD inline float j0_cos(float a) {
 #endif
 }
 
-PHI_HD inline float j0_halfcycles(float u) {
-  if (u <= 0.954929658551372f) {  // x = pi u <= 3
-    // 9.4.1 in z = (x/3)^2 = u^2 pi^2 / 9
-    const float z = (u * u) * 1.096622711232151f;
-    float p = 0.0002100f;
-    p = j0_fma(p, z, -0.0039444f);
-    p = j0_fma(p, z, 0.0444479f);
-    p = j0_fma(p, z, -0.3163866f);
-    p = j0_fma(p, z, 1.2656208f);
-    p = j0_fma(p, z, -2.2499997f);
-    return j0_fma(p, z, 1.0f);
-  }
+// Argument split between the two formulas: x = pi u = 3.
+constexpr float kJ0Split = 0.954929658551372f;
+
+// J0(pi u) for u <= kJ0Split (A&S 9.4.1).
+PHI_HD inline float j0_small(float u) {
+  // 9.4.1 in z = (x/3)^2 = u^2 pi^2 / 9
+  const float z = (u * u) * 1.096622711232151f;
+  float p = 0.0002100f;
+  p = j0_fma(p, z, -0.0039444f);
+  p = j0_fma(p, z, 0.0444479f);
+  p = j0_fma(p, z, -0.3163866f);
+  p = j0_fma(p, z, 1.2656208f);
+  p = j0_fma(p, z, -2.2499997f);
+  return j0_fma(p, z, 1.0f);
+}
+
+// J0(pi u) for u > kJ0Split (A&S 9.4.3).
+PHI_HD inline float j0_large(float u) {
   // 9.4.3 with t = 3/x, x = pi u.  With r = u^{-1/2} and s = r^2 = 1/u:
   // x^{-1/2} = r / sqrt(pi), t^k = (3/pi)^k s^k; both factors are folded
   // into the coefficients below.
@@ -91,6 +97,10 @@ PHI_HD inline float j0_halfcycles(float u) {
   // theta0 = pi (u + sum_k b_k t^k / pi) - pi/4, reduced by the cosine itself
   const float phi = j0_fma(d, s, u);
   return (r * f0) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
+}
+
+PHI_HD inline float j0_halfcycles(float u) {
+  return u <= kJ0Split ? j0_small(u) : j0_large(u);
 }
 
 }  // namespace phi

@@ -92,6 +92,17 @@ __constant__ double c_gk_node_d[15] = {
 // the FP64 path CUDA's j0.
 __device__ __forceinline__ float j0_hc(float u) { return j0_halfcycles(u); }
 __device__ __forceinline__ double j0_hc(double u) { return j0(kPi * u); }
+__device__ __forceinline__ float j0_hc_large(float u) { return j0_large(u); }
+__device__ __forceinline__ double j0_hc_large(double u) { return j0(kPi * u); }
+// Warp vote: every active lane's lowest node argument lies past the
+// small-argument formula (u > kJ0Split strictly, as j0_halfcycles tests).
+// Node arguments exceed a - Bh by at least (1 - 0.9915) Bh, far more than the
+// rounding of a - Bh, so the vote never sends a node to the wrong formula.
+// FP64 has a single formula.
+__device__ __forceinline__ bool panel_all_large(float lo, bool active) {
+  return __all_sync(0xffffffffu, !active || lo > kJ0Split);
+}
+__device__ __forceinline__ bool panel_all_large(double, bool) { return false; }
 __device__ __forceinline__ float gk_node_c(float, int j) { return c_gk_node_f[j]; }
 __device__ __forceinline__ double gk_node_c(double, int j) { return c_gk_node_d[j]; }
 // Square root for error estimates and tolerance tests only: the hardware
@@ -320,23 +331,36 @@ __device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q,
 
 // Accumulate panels [0, np) held in sh (global panel index p0 + p) for one
 // tap: Bh = 2 rho h (half-cycles of J0 per unit of the node coordinate).
+// Every node of panel p lies in [a - Bh, a + Bh], a = Bh (2 (p0 + p) + 1);
+// when that whole range is past J0's small-argument formula for every active
+// lane of the warp, the panel runs an unrolled body with the asymptotic
+// formula only (the same values j0_hc gives there), with no per-node branch.
+template <typename T, bool kLarge>
+__device__ __forceinline__ void panel_nodes(const NodeVal<T>* hp, T Bh, T a, T& kr, T& ki, T& dr,
+                                            T& di) {
+#pragma unroll
+  for (int j = 0; j < 15; ++j) {
+    const T u = fma(Bh, gk_node_c(T(0), j), a);
+    const T J = kLarge ? j0_hc_large(u) : j0_hc(u);
+    const NodeVal<T> v = hp[j];
+    kr = fma(J, v.kr, kr);
+    ki = fma(J, v.ki, ki);
+    dr = fma(J, v.dr, dr);
+    di = fma(J, v.di, di);
+  }
+}
+
 template <typename T>
-__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np, T Bh, T& kr,
-                                            T& ki, T& err) {
+__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np, T Bh, bool active,
+                                            T& kr, T& ki, T& err) {
   for (int p = 0; p < np; ++p) {
     const T a = Bh * static_cast<T>(2 * (p0 + p) + 1);
     const NodeVal<T>* hp = sh + 15 * p;
     T dr = 0, di = 0;
-#pragma unroll
-    for (int j = 0; j < 15; ++j) {
-      const T u = fma(Bh, gk_node_c(T(0), j), a);
-      const T J = j0_hc(u);
-      const NodeVal<T> v = hp[j];
-      kr = fma(J, v.kr, kr);
-      ki = fma(J, v.ki, ki);
-      dr = fma(J, v.dr, dr);
-      di = fma(J, v.di, di);
-    }
+    if (panel_all_large(a - Bh, active))
+      panel_nodes<T, true>(hp, Bh, a, kr, ki, dr, di);
+    else
+      panel_nodes<T, false>(hp, Bh, a, kr, ki, dr, di);
     err += est_sqrt(dr * dr + di * di);
   }
 }
@@ -360,14 +384,14 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
         __syncwarp();
         built = npan;
       }
-      eval_panels<T>(sh, 0, npan, Bh, kr, ki, err);
+      eval_panels<T>(sh, 0, npan, Bh, active, kr, ki, err);
     } else {
       for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
         const int nb = min(kPanelBatch, npan - p0);
         __syncwarp();
         build_nodes<T>(sh, q, npan, p0, nb, dw, lane);
         __syncwarp();
-        eval_panels<T>(sh, p0, nb, Bh, kr, ki, err);
+        eval_panels<T>(sh, p0, nb, Bh, active, kr, ki, err);
       }
       built = 0;
     }
@@ -1241,14 +1265,14 @@ __device__ C eval_chunk_capped(NodeVal<T>* sh, const QuadParams& q, T rho, bool 
         __syncwarp();
         built = npan;
       }
-      eval_panels<T>(sh, 0, npan, Bh, kr, ki, err);
+      eval_panels<T>(sh, 0, npan, Bh, active, kr, ki, err);
     } else {
       for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
         const int nb = min(kPanelBatch, npan - p0);
         __syncwarp();
         build_nodes<T>(sh, q, npan, p0, nb, dw, lane);
         __syncwarp();
-        eval_panels<T>(sh, p0, nb, Bh, kr, ki, err);
+        eval_panels<T>(sh, p0, nb, Bh, active, kr, ki, err);
       }
       built = 0;
     }
