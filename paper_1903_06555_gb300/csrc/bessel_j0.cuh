@@ -1,17 +1,18 @@
 // FP32 Bessel J0 for the w-kernel integrand, argument given in half-cycles:
 // j0_halfcycles(u) = J0(pi u), u >= 0.
 //
-// Method: Abramowitz & Stegun (1964), 9.4.1 for pi u <= 3 (polynomial in
-// (x/3)^2, |error| < 5e-8) and 9.4.3 for pi u >= 3 (J0 = x^{-1/2} f0 cos theta0
-// with f0 and theta0 polynomials in 3/x, |error| < 1.6e-8 and 7e-8 rad).
-// The phase theta0 = pi (u + sum_k b_k t^k / pi) - pi/4 is formed in FP32 and
-// handed to the hardware cosine, which reduces it by whole turns itself.  The
-// argument's own FP32 rounding (relative 6e-8, i.e. 6e-6 rad at 100 rad, the
-// largest phase a 64-tap support reaches) dominates that reduction's error, so
-// an explicit reduction in half-cycles buys no accuracy; dropping it saves ~5
-// of ~30 instructions per evaluation.  The whole evaluation costs a
-// reciprocal square root, a cosine and ~20 FMA-pipe operations.
-// Polynomials in s = 1/u absorb the factors (3/pi)^k, 1/pi and 1/sqrt(pi).
+// Method: Abramowitz & Stegun (1964) 9.4.1 for pi u <= 3 (polynomial in
+// (x/3)^2, |error| < 5e-8); for pi u > 3 the modulus/phase form
+// J0 = M0 cos theta0 (A&S 9.2.17) with sqrt(u) M0 and the phase correction
+// as degree-4 polynomials in 1/u^2 (the parities of their Hankel expansions,
+// A&S 9.2.28-9.2.31), coefficients fitted by j0_fit.py in this directory
+// (|error| < 5.2e-8).
+// The phase theta0 = pi (u + D/u) - pi/4 is formed in FP32 and handed to the
+// hardware cosine, which reduces it by whole turns itself.  The argument's own
+// FP32 rounding (relative 6e-8, i.e. 6e-6 rad at 100 rad, the largest phase a
+// 64-tap support reaches) dominates that reduction's error, so an explicit
+// reduction buys no accuracy.  The large-argument evaluation costs a
+// reciprocal square root, a cosine and ~15 FMA-pipe operations.
 #pragma once
 
 #ifndef PHI_HD
@@ -69,34 +70,26 @@ PHI_HD inline float j0_small(float u) {
   return j0_fma(p, z, 1.0f);
 }
 
-// J0(pi u) for u > kJ0Split (A&S 9.4.3).
+// J0(pi u) for u > kJ0Split: u^{-1/2} F(q) cos(pi (u + D(q)/u) - pi/4), q = 1/u^2,
+// the modulus/phase form of A&S 9.2.17 with F and D the degree-4 L-infinity
+// fits that j0_fit.py computes (J0 error <= 3.6e-8 from F, 1.6e-8 from D).
 PHI_HD inline float j0_large(float u) {
-  // 9.4.3 with t = 3/x, x = pi u.  With r = u^{-1/2} and s = r^2 = 1/u:
-  // x^{-1/2} = r / sqrt(pi), t^k = (3/pi)^k s^k; both factors are folded
-  // into the coefficients below.
   const float r = j0_rsqrt(u);
-  const float s = r * r;
-  const float c1 = 0.954929658551372f;  // 3 / pi
-  const float c2 = c1 * c1, c3 = c2 * c1, c4 = c3 * c1, c5 = c4 * c1, c6 = c5 * c1;
-  const float isp = 0.564189583547756f;  // 1 / sqrt(pi)
-  float f0 = 0.00014476f * c6 * isp;
-  f0 = j0_fma(f0, s, -0.00072805f * c5 * isp);
-  f0 = j0_fma(f0, s, 0.00137237f * c4 * isp);
-  f0 = j0_fma(f0, s, -0.00009512f * c3 * isp);
-  f0 = j0_fma(f0, s, -0.00552740f * c2 * isp);
-  f0 = j0_fma(f0, s, -0.00000077f * c1 * isp);
-  f0 = j0_fma(f0, s, 0.79788456f * isp);
-  // (theta0 - x + pi/4) / pi = sum_k b_k t^k / pi, k >= 1
-  const float ip = 0.318309886183791f;
-  float d = 0.00013558f * c6 * ip;
-  d = j0_fma(d, s, -0.00029333f * c5 * ip);
-  d = j0_fma(d, s, -0.00054125f * c4 * ip);
-  d = j0_fma(d, s, 0.00262573f * c3 * ip);
-  d = j0_fma(d, s, -0.00003954f * c2 * ip);
-  d = j0_fma(d, s, -0.04166397f * c1 * ip);
-  // theta0 = pi (u + sum_k b_k t^k / pi) - pi/4, reduced by the cosine itself
+  const float s = r * r;   // 1 / u
+  const float q = s * s;   // 1 / u^2
+  float f = 2.949163237e-05f;
+  f = j0_fma(f, q, -1.386496738e-04f);
+  f = j0_fma(f, q, 4.440745370e-04f);
+  f = j0_fma(f, q, -2.846068740e-03f);
+  f = j0_fma(f, q, 4.501580035e-01f);
+  float d = -1.531106734e-05f;
+  d = j0_fma(d, q, 6.988119170e-05f);
+  d = j0_fma(d, q, -1.853455306e-04f);
+  d = j0_fma(d, q, 6.629692300e-04f);
+  d = j0_fma(d, q, -1.266485270e-02f);
+  // theta0 = pi (u + D / u) - pi/4, reduced by the cosine itself
   const float phi = j0_fma(d, s, u);
-  return (r * f0) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
+  return (r * f) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
 }
 
 PHI_HD inline float j0_halfcycles(float u) {
