@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mwa", choices=["mwa", "serve", "plan"],
+    ap.add_argument("--workload", default="mwa", choices=["mwa", "serve", "plan", "precision", "diff"],
                     help="mwa: the headline operator benchmark; serve: the serving stream; "
                          "plan: Algorithm 1 and the fold at the paper's scale")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -744,6 +744,131 @@ def run_plan_study(args):
     print(json.dumps(line), flush=True)
 
 
+def timed_ms(fn, steps, warmup):
+    """Mean milliseconds of fn() over `steps` calls after `warmup`, CUDA
+    events on the current stream."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for a, b in ev:
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def run_precision(args):
+    """The precision study (4096^2 image, 8192^2 grid, 17.5M visibilities,
+    |w| <= 1500, 32 stacks, fold on): the FP32 path (FP64 chirp phase) timed
+    at full size; FP32 and FP64 (quadrature tol 1e-12) on a 20,000-visibility
+    sub-observation with the full plan's centres and supports, i.e. the same
+    operator, timed and compared."""
+    import paper_1903_06555_gb300 as phi
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = W.precision_study()
+    uvw = W.uvw_for(wl)
+    kw = dict(image_n=wl.image_n, fov_rad=math.radians(wl.fov_deg), n_stacks=wl.n_stacks,
+              conj_fold=int(wl.conj_fold))
+    x_np = W.point_sources(wl.image_n, wl.n_sources, wl.seed)
+    plan = phi.Plan(torch.from_numpy(uvw).to(dev), **kw)
+    info = plan.info()
+    x32 = torch.from_numpy(x_np).to(dev, torch.float32)
+    y = torch.from_numpy(W.random_vis(len(uvw), 4)).to(dev, torch.complex64)
+    ms32 = timed_ms(lambda: (plan.degrid(x32), plan.grid(y)), args.steps, args.warmup)
+    plan.close()
+    sel = np.sort(np.random.default_rng(2).choice(len(uvw), 20000, replace=False))
+    sub = torch.from_numpy(np.ascontiguousarray(uvw[sel])).to(dev)
+    fixed = dict(centres=info["wbar"], stack_jw=info["jw"], **kw)
+    p32 = phi.Plan(sub, **fixed)
+    p64 = phi.Plan(sub, precision="f64", quad_rel_tol=1e-12, quad_abs_tol=1e-12, **fixed)
+    n_sub = p64.info()["n_kept"]
+    x64 = x32.double()
+    ys = y[torch.from_numpy(sel).to(dev)]
+    ms_sub32 = timed_ms(lambda: (p32.degrid(x32), p32.grid(ys)), 3, 1)
+    ms_sub64 = timed_ms(lambda: (p64.degrid(x64), p64.grid(ys.to(torch.complex128))), 1, 1)
+
+    def rel(a, b):
+        return float(torch.linalg.vector_norm(a.to(b.dtype) - b) / torch.linalg.vector_norm(b))
+    line = {"metric": "precision study: FP32 (FP64 chirp phase) vs FP64, degrid+grid",
+            "workload": f"{wl.name}: {wl.image_n}^2 image, {info['npad']}^2 grid, "
+                        f"{len(uvw)} visibilities, {wl.n_stacks} stacks, |w| <= {wl.uvw['wmax']:g}",
+            "fp32_full": {"vis_per_s": info["n_kept"] / (ms32 / 1e3), "ms_per_step": ms32,
+                          "n_kept": info["n_kept"], "max_jw": info["max_jw"]},
+            "sub_observation": {
+                "n_kept": n_sub,
+                "fp32_vis_per_s": n_sub / (ms_sub32 / 1e3), "fp64_vis_per_s": n_sub / (ms_sub64 / 1e3),
+                "fp32_vs_fp64_rel_l2": {"degrid": rel(p32.degrid(x32), p64.degrid(x64)),
+                                        "grid": rel(p32.grid(ys), p64.grid(ys.to(torch.complex128)))},
+                "note": "same centres and supports as the full plan; FP64 path at quadrature "
+                        "tol 1e-12 (parity-tested against the FP64 oracle to 1e-10)"},
+            "paper_context": "Paper I: 17.5M visibilities"}
+    print(json.dumps(line), flush=True)
+
+
+def run_diff(args):
+    """The differentiable workload (4096^2 image, 8192^2 grid, 10M visibilities,
+    16 stacks): L = 1/2 ||Phi x - y||^2 through autograd.PhiDegrid (backward =
+    phi_grid), timed per forward+backward; the directional derivative on 64
+    random pixels against a central difference; 20 power iterations for
+    ||Phi||^2 and 20 gradient-descent steps."""
+    import paper_1903_06555_gb300 as phi
+    from paper_1903_06555_gb300 import autograd as PA, solvers
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = W.differentiable()
+    uvw = W.uvw_for(wl)
+    plan = phi.Plan(torch.from_numpy(uvw).to(dev), image_n=wl.image_n,
+                    fov_rad=math.radians(wl.fov_deg), n_stacks=wl.n_stacks,
+                    conj_fold=int(wl.conj_fold), max_support=192)
+    info = plan.info()
+    x_true = torch.from_numpy(W.point_sources(wl.image_n, wl.n_sources, wl.seed)).to(dev).float()
+    y = plan.degrid(x_true)
+    x = (0.5 * x_true).requires_grad_(True)
+
+    def fwd_bwd():
+        x.grad = None
+        loss = 0.5 * torch.sum(torch.abs(PA.degrid(x, plan) - y) ** 2)
+        loss.backward()
+    ms = timed_ms(fwd_bwd, args.steps, args.warmup)
+    rng = np.random.default_rng(3)
+    n = wl.image_n
+    v = torch.zeros(n * n, device=dev)
+    v[torch.from_numpy(rng.choice(n * n, 64, replace=False)).to(dev)] = \
+        torch.from_numpy(rng.standard_normal(64)).to(dev).float()
+    v = v.view(n, n)
+    fwd_bwd()
+    g_dir = float(torch.sum(x.grad.double() * v.double()))
+
+    def L(t):
+        return 0.5 * float(torch.sum(torch.abs((plan.degrid(t) - y).to(torch.complex128)) ** 2))
+    eps = 1e-2 * float(x_true.abs().max())
+    fd = (L(x.detach() + eps * v) - L(x.detach() - eps * v)) / (2 * eps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lam, _ = solvers.power_method(plan, 20)
+    torch.cuda.synchronize()
+    t_pm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, losses = solvers.least_squares(plan, y, steps=20, step=1.0 / lam)
+    torch.cuda.synchronize()
+    t_gd = time.perf_counter() - t0
+    line = {"metric": "differentiable operator: forward+backward of 1/2||Phi x - y||^2",
+            "workload": f"{wl.name}: {wl.image_n}^2 image, {info['npad']}^2 grid, "
+                        f"{len(uvw)} visibilities, {wl.n_stacks} stacks",
+            "fwd_bwd_ms": ms, "vis_per_s": info["n_kept"] / (ms / 1e3),
+            "finite_difference": {"directional_grad": g_dir, "central_difference": fd,
+                                  "rel_diff": abs(fd - g_dir) / abs(g_dir),
+                                  "direction": "64 random pixels, eps = 1e-2 max|x|, FP32 path"},
+            "power_method": {"iters": 20, "norm_sq": lam, "seconds": t_pm},
+            "gradient_descent": {"steps": 20, "seconds": t_gd, "loss_first": losses[0],
+                                 "loss_last": losses[-1],
+                                 "monotone": all(b <= a * (1 + 1e-6)
+                                                 for a, b in zip(losses, losses[1:]))}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -755,6 +880,12 @@ def main():
     elif args.workload == "plan":
         if rank == 0:
             run_plan_study(args)
+    elif args.workload == "precision":
+        if rank == 0:
+            run_precision(args)
+    elif args.workload == "diff":
+        if rank == 0:
+            run_diff(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:
