@@ -226,6 +226,33 @@ def test_visibilities_on_grid_points_match_oracle(precision):
     assert O.rel_l2(plan.grid(to_t(yr, cd)).cpu().numpy(), O.grid(op, yr)) < tol
 
 
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_maximum_support_matches_oracle(precision):
+    """J_w = 64, the default cap: 4,096 taps per visibility with radii up to
+    ~45 pixels, so the quadrature needs more than 16 panels per chunk (the
+    batched node path).  One stack, |dw| up to 29.5 / c_support."""
+    geo = oracle_geo(128)
+    rng = np.random.default_rng(91)
+    n = 20
+    r = 40.0 * np.sqrt(rng.random(n))
+    t = rng.uniform(0, 2 * np.pi, n)
+    wm = 29.5 / geo.c_support
+    w = np.concatenate([np.linspace(-wm, wm, n // 2), -np.linspace(-wm, wm, n // 2)])
+    uvw = np.column_stack([r * np.cos(t), r * np.sin(t), w])
+    op = O.make_plan(uvw, geo, 1, False)
+    assert op.jw.max() == 64
+    plan = gpu_plan(uvw, geo, 1, False, precision)
+    assert plan.info()["jw"] == [64]
+    rd, cd = (torch.float64, torch.complex128) if precision == "f64" else (torch.float32, torch.complex64)
+    tol = TOL64 if precision == "f64" else TOL32
+    x = W.point_sources(128, 20, 92)
+    yr = W.random_vis(n, 93)
+    assert O.rel_l2(plan.degrid(to_t(x, rd)).cpu().numpy(), O.degrid(op, x)) < tol
+    assert O.rel_l2(plan.grid(to_t(yr, cd)).cpu().numpy(), O.grid(op, yr)) < tol
+    bad, _ = plan.stats()
+    assert bad == 0
+
+
 # ----------------------------------------------------------------------------- full size
 
 @pytest.fixture(scope="module")
