@@ -506,7 +506,10 @@ def run_ours(args, ws, rank, local):
         "kernel_mode": args.kernel_mode,
         "table": table_info,
         "e2e": e2e,
-        "gpu_launches": int(4 * sum(1 for c in info["counts"] if c > 0) * args.steps),
+        # this library's kernels in the timed steps (prep, fused degrid, fused
+        # grid, finish: one each per stack group); cuFFT's and the memsets are
+        # not counted
+        "gpu_launches": int(sum(stages[k][1] for k in ("prep", "degrid", "grid", "finish"))),
         "clocks": clocks,
         "wall_s_timed": wall,
     }
