@@ -124,3 +124,31 @@ def test_table_close_to_quadrature_at_full_size():
     scale = torch.abs(ys["quadrature"]).max()
     assert (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(ys["quadrature"])).item() < 1e-4
     assert (torch.abs(d).max() / scale).item() < 1e-4
+
+
+def test_table_at_maximum_support_matches_oracle():
+    """J_w = 64 (the default cap), radii up to ~45 pixels: the far end of the
+    planes and the last interval.  FP32 against the oracle's table path at the
+    same sample points (table_tol 1e-2 keeps the oracle's table small; the
+    oracle samples at tol 1e-9, below the FP32 gate)."""
+    geo = O.Geometry(128, 2.0, math.radians(20.0), 4.0, tol_rel=1e-9, tol_abs=1e-9)
+    rng = np.random.default_rng(91)
+    n = 20
+    r = 40.0 * np.sqrt(rng.random(n))
+    t = rng.uniform(0, 2 * np.pi, n)
+    wm = 29.5 / geo.c_support
+    w = np.concatenate([np.linspace(-wm, wm, n // 2), -np.linspace(-wm, wm, n // 2)])
+    uvw = np.column_stack([r * np.cos(t), r * np.sin(t), w])
+    op = O.make_plan(uvw, geo, 1, False)
+    assert op.jw.max() == 64
+    tab = O.make_table(op, 1e-2)
+    plan = phi.Plan(torch.from_numpy(uvw), image_n=128, fov_rad=geo.fov, n_stacks=1,
+                    kernel_mode="table", table_tol=1e-2)
+    info = plan.info()
+    assert info["jw"] == [64] and info["table_n_rho"] == tab.nr and info["table_n_w"] == tab.nw
+    x = W.point_sources(128, 20, 92)
+    yr = W.random_vis(n, 93)
+    y = plan.degrid(torch.from_numpy(x).cuda().float()).cpu().numpy()
+    assert O.rel_l2(y, O.degrid_table(op, x, tab)) < 1e-5
+    xg = plan.grid(torch.from_numpy(yr).cuda().to(torch.complex64)).cpu().numpy()
+    assert O.rel_l2(xg, O.grid_table(op, yr, tab)) < 1e-5
