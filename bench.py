@@ -39,6 +39,8 @@ METRIC = "w-corrected visibilities/s (degrid+grid) at <=1e-5 rel err vs FP64; p5
 UNIT = "vis/s"
 FLOPS_PER_TAP_NODE = 36.0     # J0 by a rational/asymptotic approximation (28) + 2 weighted complex MACs (8)
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM per clock (Blackwell)
+RADIAL_POINTS = 16            # Chebyshev points per piece, FP32 radial mode
+RADIAL_FLOPS_PER_TAP = 96     # 15 Clenshaw steps x (2 FMA + 2 subtractions) + the last step
 NUM_SMS = 152
 
 
@@ -61,7 +63,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cycles-per-panel", type=float, default=0.0,
                     help="a-priori quadrature panel width in integrand cycles (0: library default)")
-    ap.add_argument("--kernel-mode", default="quadrature", choices=["quadrature", "table"],
+    ap.add_argument("--kernel-mode", default="quadrature", choices=["quadrature", "table", "radial"],
                     help="quadrature: every tap integrated (the hot path); table: pre-sampled "
                          "1-D w-planes with bilinear interpolation (Sec. 5.1.1)")
     ap.add_argument("--table-tol", type=float, default=1e-4)
@@ -414,19 +416,25 @@ def run_ours(args, ws, rank, local):
     p50 = statistics.median(lat)
     p99 = lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)]
 
-    table_info = None
-    if args.kernel_mode == "table":
+    table_info = radial_info = None
+    if args.kernel_mode != "quadrature":
         qdesc = dict(desc, kernel_mode="quadrature")
         qplan = phi.Plan(uvw, **qdesc)
         yq = qplan.degrid(x)
         yt = plan.degrid(x)
         qplan.close()
-        table_info = {"table_tol": args.table_tol, "n_rho": info["table_n_rho"],
-                      "n_w": info["table_n_w"], "h_rho": info["table_h_rho"],
-                      "h_w": info["table_h_w"],
-                      "bytes": 16 * info["table_n_rho"] * (info["table_n_w"] - 1),
-                      "rel_l2_vs_quadrature_path": float(torch.linalg.vector_norm(yt - yq) /
-                                                         torch.linalg.vector_norm(yq))}
+        rel_q = float(torch.linalg.vector_norm(yt - yq) / torch.linalg.vector_norm(yq))
+        if args.kernel_mode == "table":
+            table_info = {"table_tol": args.table_tol, "n_rho": info["table_n_rho"],
+                          "n_w": info["table_n_w"], "h_rho": info["table_h_rho"],
+                          "h_w": info["table_h_w"],
+                          "bytes": 16 * info["table_n_rho"] * (info["table_n_w"] - 1),
+                          "rel_l2_vs_quadrature_path": rel_q}
+        else:
+            radial_info = {"piece_width_px": 2.0 / info["window_radius"],
+                           "points_per_piece": RADIAL_POINTS,
+                           "quadrature_points_per_vis": tap_nodes / (2 * args.steps * n_kept),
+                           "rel_l2_vs_quadrature_path": rel_q}
 
     # roofline: the dominant kernel (fused quadrature + degrid or + grid)
     counts = load_oracle_counts()
@@ -461,6 +469,19 @@ def run_ours(args, ws, rank, local):
                              "8 B per grid cell covered by a kernel box, the plane pairs once "
                              "per launch; the kernel is L1/TEX bound (92% of that pipe in ncu), "
                              "far below the HBM roofline"}
+    elif args.kernel_mode == "radial":
+        # executed work: the quadrature at the Chebyshev points (tap-nodes) and
+        # the series evaluated at every tap; degrid and grid do the same work
+        per_launch = (tap_nodes * FLOPS_PER_TAP_NODE + taps * RADIAL_FLOPS_PER_TAP) / (2.0 * n_dom)
+        ach = per_launch / ((ms_dom / n_dom) / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": f"vis_radial_kernel ({dom})", "achieved": ach,
+                "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32,
+                "traffic": profiled_traffic("radial_" + dom),
+                "peak_note": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
+                             f"{sm_mhz:.0f} MHz (recipe unit counts, max clock)",
+                "work_note": f"{FLOPS_PER_TAP_NODE:.0f} flops per quadrature tap-node at the "
+                             f"Chebyshev points + {RADIAL_FLOPS_PER_TAP} flops per tap for its "
+                             "series (executed work, not the oracle's per-tap count)"}
     else:
         roof = {"bound": "alu", "kernel": f"vis_kernel ({dom})", "achieved": achieved,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
@@ -505,6 +526,7 @@ def run_ours(args, ws, rank, local):
         "roofline": roof,
         "kernel_mode": args.kernel_mode,
         "table": table_info,
+        "radial": radial_info,
         "e2e": e2e,
         # this library's kernels in the timed steps (prep, fused degrid, fused
         # grid, finish: one each per stack group); cuFFT's and the memsets are

@@ -81,7 +81,11 @@ enum phi_precision {
 
 enum phi_kernel_mode {
   PHI_KERNEL_QUADRATURE = 0,  /* every tap by adaptive quadrature (Sec. 3.1)         */
-  PHI_KERNEL_TABLE = 1        /* pre-sampled 1-D w-planes, bilinear (Sec. 5.1.1)       */
+  PHI_KERNEL_TABLE = 1,       /* pre-sampled 1-D w-planes, bilinear (Sec. 5.1.1)       */
+  PHI_KERNEL_RADIAL = 2       /* per visibility: the same quadrature at Chebyshev radii,
+                                 every tap from the resulting series in rho (no
+                                 counterpart in the paper; same operator within the
+                                 quadrature tolerance)                                 */
 };
 
 enum phi_support_rule {
@@ -157,7 +161,16 @@ int phi_plan_desc_default(phi_plan_desc* desc);
  * 0 <= w <= max |w - wbar_k| (positive only: -w is the conjugate), computed
  * by the same adaptive quadrature, stored in pairs of adjacent w-planes;
  * degrid and grid then interpolate every tap bilinearly instead of
- * integrating it.
+ * integrating it.  With PHI_KERNEL_RADIAL nothing extra is stored: for each
+ * visibility the fused kernels integrate [GC](rho, dw_i) by the same
+ * quadrature at the Chebyshev points of equal pieces of [0, rho_max]
+ * (pieces of 2 / R grid pixels, 16 points each in FP32, 24 in FP64; the
+ * kernel is band-limited to R cycles per pixel in rho, R the window radius)
+ * and evaluate every tap from its piece's Chebyshev series; a piece whose
+ * two trailing coefficients exceed the quadrature tolerance counts as
+ * unconverged (phi_plan_stats).  PHI_ERR_SUPPORT if the per-warp series
+ * storage for the largest support would exceed the shared memory of a
+ * thread block.
  *   uvw_dev:     n_vis x 3 float64 (u, v, w in wavelengths), row-major, device.
  *   weights_dev: n_vis float64 weights W_i (Eq. matrix_equation), or NULL for 1.
  *   n_vis:       >= 0.

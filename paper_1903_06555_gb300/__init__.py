@@ -31,7 +31,7 @@ PHI_OK, PHI_ERR_ARG, PHI_ERR_OOM, PHI_ERR_CUDA, PHI_ERR_HORIZON, PHI_ERR_SUPPORT
     PHI_ERR_TIMEOUT, PHI_ERR_STATE = range(8)
 PHI_F32, PHI_F64 = 0, 1
 PHI_SUPPORT_STACK, PHI_SUPPORT_VIS = 0, 1
-PHI_KERNEL_QUADRATURE, PHI_KERNEL_TABLE = 0, 1
+PHI_KERNEL_QUADRATURE, PHI_KERNEL_TABLE, PHI_KERNEL_RADIAL = 0, 1, 2
 STAGES = ("prep", "fft", "degrid", "grid", "finish", "clear")
 NUM_STAGES = len(STAGES)
 
@@ -178,7 +178,8 @@ def default_desc(**kw) -> PlanDesc:
         if k == "support_rule" and isinstance(v, str):
             v = {"stack": PHI_SUPPORT_STACK, "vis": PHI_SUPPORT_VIS}[v]
         if k == "kernel_mode" and isinstance(v, str):
-            v = {"quadrature": PHI_KERNEL_QUADRATURE, "table": PHI_KERNEL_TABLE}[v]
+            v = {"quadrature": PHI_KERNEL_QUADRATURE, "table": PHI_KERNEL_TABLE,
+                 "radial": PHI_KERNEL_RADIAL}[v]
         if not hasattr(d, k):
             raise TypeError(f"unknown descriptor field {k}")
         setattr(d, k, type(getattr(d, k))(v))

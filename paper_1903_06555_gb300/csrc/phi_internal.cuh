@@ -86,6 +86,25 @@ template <typename T> struct NodeVal;
 template <> struct __align__(16) NodeVal<float> { float kr, ki, dr, di; };
 template <> struct __align__(16) NodeVal<double> { double kr, ki, dr, di; };
 
+// Radial interpolation mode (PHI_KERNEL_RADIAL): Chebyshev points per piece
+// of [0, rho_max], by precision (interpolation error ~1e-7 and ~4e-14 of
+// K(0) at pieces of 2 / R pixels).
+template <typename T> struct RadialN;
+template <> struct RadialN<float> { static constexpr int n = 16; };
+template <> struct RadialN<double> { static constexpr int n = 24; };
+
+// Kernel-side view of the radial mode's tables: piece width L (grid pixels)
+// and 1 / L; x1[j] = (1 + cos(pi (j + 1/2) / n)) / 2, the Chebyshev points
+// mapped to [0, 1]; dct[j n + m] = cos(pi m (j + 1/2) / n); buf = complex
+// values of series storage per warp (pieces x (n + 1)).
+template <typename T>
+struct RadialView {
+  T L, inv_L;
+  const T* x1;
+  const T* dct;
+  int buf;
+};
+
 // Kernel-side constants of one plan.
 struct QuadParams {
   double R;               // window radius (r units)
@@ -160,6 +179,11 @@ struct Plan {
   std::vector<uint8_t> stack_staged;    // table path: stage this stack's grid tiles
   int tile = 32;
   int tiles_per_row = 0;
+  // radial interpolation mode (PHI_KERNEL_RADIAL): tables of precision T
+  // (x1[n] then dct[n * n]), piece width, series storage per warp
+  void* radial_tab = nullptr;
+  double radial_L = 0;
+  int radial_buf = 0;
 
   QuadParams quad() const {
     QuadParams q;
@@ -205,6 +229,7 @@ void timer_end(Plan& p, long idx, int stage, cudaStream_t s);
 int launch_node_tables(Plan& p, cudaStream_t s);
 int launch_pixel_tables(Plan& p, cudaStream_t s);
 int build_kernel_table(Plan& p, cudaStream_t s);
+int build_radial_tables(Plan& p, cudaStream_t s);
 
 }  // namespace phi
 

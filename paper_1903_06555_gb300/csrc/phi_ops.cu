@@ -867,6 +867,216 @@ __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__
 }
 
 // ---------------------------------------------------------------------------
+// Radial interpolation mode (PHI_KERNEL_RADIAL)
+// ---------------------------------------------------------------------------
+
+// For one visibility, [GC](., dw) is an even function of rho band-limited to
+// R cycles per grid pixel (the integral runs over r <= R).  The warp
+// integrates it by eval_chunk's quadrature at the Chebyshev points of pieces
+// of [0, rho_max] of width L = 2 / R, turns each piece's values into its
+// Chebyshev coefficients in shared memory (in place), and evaluates every tap
+// from its piece's series by Clenshaw's recurrence.  A piece whose two
+// trailing coefficients exceed the tolerance is counted as unconverged.
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel(
+    const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
+    const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
+    C* __restrict__ vis_out, QuadParams q, RadialView<T> rv,
+    const int32_t* __restrict__ stack_slot, unsigned long long* head,
+    unsigned long long* stats, int batch) {
+  constexpr int NC = RadialN<T>::n;   // Chebyshev points per piece
+  constexpr int NS = NC + 1;          // stride of a piece (offsets the banks)
+  constexpr int PPW = 32 / NC;        // pieces transformed per warp pass
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
+  C* ser = reinterpret_cast<C*>(smem_raw + (blockDim.x >> 5) * kNodeBatch * sizeof(NodeVal<T>)) +
+           warp * rv.buf;
+  const int max_pieces = rv.buf / NS;
+  unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
+  const int npad = q.npad;
+  const unsigned long long kBatch = static_cast<unsigned long long>(batch);
+  unsigned long long next = 0, stop = 0;
+  while (true) {
+    if (next == stop) {
+      unsigned long long i0 = 0;
+      if (lane == 0) i0 = atomicAdd(head, kBatch);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+      next = i0;
+      stop = min(i0 + kBatch, static_cast<unsigned long long>(n));
+      if (next >= stop) break;
+    }
+    const unsigned long long i = next++;
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw;
+    const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
+    const int half = Jw / 2;
+    const T fu = r.fu, fv = r.fv;
+    const float adw = static_cast<float>(fabs(r.dw));
+    const uint32_t pm = perm[i];
+    C yv = cmake<C>(0.0, 0.0);
+    if (kGrid) {
+      C v = vis_in[pm & 0x7fffffffu];
+      if (pm >> 31) v.y = -v.y;
+      yv.x = v.x * static_cast<T>(r.weight);
+      yv.y = v.y * static_cast<T>(r.weight);
+    }
+    // farthest tap: |u offset| <= max(half - fu, fu + half - 1), likewise in v;
+    // the piece count is clamped to the storage the plan sized for its
+    // largest support (a rounding excess is extrapolated by the last piece)
+    const T mu = fmax(static_cast<T>(half) - fu, fu + static_cast<T>(half - 1));
+    const T mv = fmax(static_cast<T>(half) - fv, fv + static_cast<T>(half - 1));
+    const T pf = ceil(sqrt(mu * mu + mv * mv) * rv.inv_L);
+    int pieces = 1;
+    if (pf >= static_cast<T>(max_pieces)) pieces = max_pieces;
+    else if (pf > T(1)) pieces = static_cast<int>(pf);
+    const int npts = pieces * NC;
+    int built = 0;
+    // 1. the kernel at the Chebyshev points, 32 at a time in increasing rho
+    for (int k0 = 0; k0 < npts; k0 += 32) {
+      const int k = k0 + lane;
+      const bool active = k < npts;
+      const int kk = active ? k : npts - 1;   // idle lanes repeat the last point
+      const int pc = kk / NC, j = kk - pc * NC;
+      const T rho = rv.L * (static_cast<T>(pc) + rv.x1[j]);
+      T rmax = rho;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      const int npan = initial_panels(q, static_cast<float>(rmax), adw);
+      bool ok = true;
+      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, built, ok, lane, my_nodes);
+      if (active) {
+        ser[pc * NS + j] = K;
+        if (!ok) ++my_bad;
+      }
+    }
+    __syncwarp();
+    // 2. c_m = (2 - [m == 0]) / NC sum_j f_j cos(pi m (j + 1/2) / NC), in place
+    for (int p0 = 0; p0 < pieces; p0 += PPW) {
+      const int pc = p0 + lane / NC, m = lane - (lane / NC) * NC;
+      const bool on = lane < PPW * NC && pc < pieces;
+      C c = cmake<C>(0.0, 0.0);
+      if (on) {
+        const C* f = ser + pc * NS;
+        const T* dc = rv.dct + m;
+#pragma unroll 4
+        for (int j = 0; j < NC; ++j) {
+          const T t = dc[j * NC];
+          const C v = f[j];
+          c.x = fma(v.x, t, c.x);
+          c.y = fma(v.y, t, c.y);
+        }
+        const T sc = (m == 0 ? T(1) : T(2)) / static_cast<T>(NC);
+        c.x *= sc;
+        c.y *= sc;
+      }
+      __syncwarp();
+      if (on) ser[pc * NS + m] = c;
+      __syncwarp();
+    }
+    for (int pc = lane; pc < pieces; pc += 32) {
+      const C* c = ser + pc * NS;
+      T cmax = 0;
+      for (int m = 0; m < NC; ++m) cmax = fmax(cmax, est_sqrt(c[m].x * c[m].x + c[m].y * c[m].y));
+      const T tail = est_sqrt(c[NC - 1].x * c[NC - 1].x + c[NC - 1].y * c[NC - 1].y) +
+                     est_sqrt(c[NC - 2].x * c[NC - 2].x + c[NC - 2].y * c[NC - 2].y);
+      if (!(tail <= fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * cmax))) ++my_bad;
+    }
+    // 3. every tap from its piece's series; taps t = b Jw + a in raster order,
+    // advanced by 32 per chunk without a division per tap
+    C accv = cmake<C>(0.0, 0.0);
+    const int ntap = Jw * Jw;
+    int a = lane % Jw, b = lane / Jw;
+    const int step_b = 32 / Jw, step_a = 32 % Jw;
+    T du_ = fu - static_cast<T>(a - half + 1), dv_ = fv - static_cast<T>(b - half + 1);
+    const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
+    const T fJw = static_cast<T>(Jw);
+    const int last = pieces - 1;
+    const T last_f = static_cast<T>(last);
+    for (int t0 = 0; t0 < ntap; t0 += 32) {
+      const int t = t0 + lane;
+      if (t < ntap) {
+        const int ou = a - half + 1, ov = b - half + 1;
+        const T rho = sqrt(du_ * du_ + dv_ * dv_);
+        int ip;
+        T fr;
+        table_index(rho * rv.inv_L, last, last_f, ip, fr);
+        const T x = fma(T(2), fr, T(-1));
+        const T x2 = x + x;
+        const C* c = ser + ip * NS;
+        // Clenshaw: b_m = 2 x b_{m+1} - b_{m+2} + c_m;  K = x b_1 - b_2 + c_0
+        T b1x = 0, b1y = 0, b2x = 0, b2y = 0;
+#pragma unroll
+        for (int m = NC - 1; m >= 1; --m) {
+          const C cm = c[m];
+          const T nx = fma(x2, b1x, cm.x - b2x);
+          const T ny = fma(x2, b1y, cm.y - b2y);
+          b2x = b1x;
+          b2y = b1y;
+          b1x = nx;
+          b1y = ny;
+        }
+        const C c0 = c[0];
+        C K;
+        K.x = fma(x, b1x, c0.x - b2x);
+        K.y = fma(x, b1y, c0.y - b2y);
+        ++my_taps;
+        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                           wrap_index(r.bu + ou, npad);
+        if (kGrid) {
+          C add;
+          add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
+          add.y = K.x * yv.y - K.y * yv.x;
+          atomic_add_c(grid_out + gi, add);
+        } else {
+          const C g = grid_in[gi];
+          accv.x += K.x * g.x - K.y * g.y;
+          accv.y += K.x * g.y + K.y * g.x;
+        }
+      }
+      a += step_a;
+      b += step_b;
+      du_ -= fstep_a;
+      dv_ -= fstep_b;
+      if (a >= Jw) {
+        a -= Jw;
+        ++b;
+        du_ += fJw;
+        dv_ -= T(1);
+      }
+    }
+    // the series storage is rewritten by the next visibility's samples
+    __syncwarp();
+    if (!kGrid) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
+        accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
+      }
+      if (lane == 0) {
+        C out;
+        out.x = accv.x * static_cast<T>(r.weight);
+        out.y = accv.y * static_cast<T>(r.weight);
+        if (pm >> 31) out.y = -out.y;
+        vis_out[pm & 0x7fffffffu] = out;
+      }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
+    my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
+    my_nodes += __shfl_xor_sync(0xffffffffu, my_nodes, o);
+  }
+  if (lane == 0 && my_taps) {
+    atomicAdd(stats, my_bad);
+    atomicAdd(stats + 1, my_taps);
+    atomicAdd(stats + 3, my_nodes);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Host side of the operator
 // ---------------------------------------------------------------------------
 namespace {
@@ -881,6 +1091,53 @@ int blocks_for_vis(const Plan& p, size_t smem) {
       per_sm < 1)
     per_sm = 1;
   return per_sm * p.num_sms;
+}
+
+template <typename T, typename C>
+size_t radial_smem(const Plan& p) {
+  return (kVisThreads / 32) *
+         (kNodeBatch * sizeof(NodeVal<T>) + static_cast<size_t>(p.radial_buf) * sizeof(C));
+}
+
+template <typename T, typename C>
+RadialView<T> radial_view(const Plan& p) {
+  RadialView<T> v;
+  v.L = static_cast<T>(p.radial_L);
+  v.inv_L = static_cast<T>(1.0 / p.radial_L);
+  v.x1 = static_cast<const T*>(p.radial_tab);
+  v.dct = static_cast<const T*>(p.radial_tab) + RadialN<T>::n;
+  v.buf = p.radial_buf;
+  return v;
+}
+
+// Chebyshev tables of the radial mode in the plan's precision, the piece
+// width L = 2 / R and the series storage per warp for the largest support
+// (every tap of a J_w box lies within sqrt(2) J_w / 2 of the visibility).
+template <typename T, typename C>
+int build_radial_tables_t(Plan& p, cudaStream_t s) {
+  constexpr int n = RadialN<T>::n;
+  std::vector<T> tab(n + n * n);
+  for (int j = 0; j < n; ++j) {
+    const double th = kPi * (j + 0.5) / n;
+    tab[j] = static_cast<T>(0.5 * (1.0 + std::cos(th)));
+    for (int m = 0; m < n; ++m) tab[n + j * n + m] = static_cast<T>(std::cos(m * th));
+  }
+  p.radial_L = 2.0 / p.R;
+  const double rmax = std::sqrt(2.0) * std::max(p.max_jw, p.d.support) / 2.0;
+  const int pieces = std::max(1, static_cast<int>(std::ceil(rmax / p.radial_L)));
+  p.radial_buf = pieces * (n + 1);
+  int dev = 0, optin = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (radial_smem<T, C>(p) > static_cast<size_t>(optin)) return PHI_ERR_SUPPORT;
+  void* raw = nullptr;
+  PHI_CUDA_TRY(cudaMalloc(&raw, sizeof(T) * tab.size()));
+  p.radial_tab = raw;
+  p.device_bytes += static_cast<int64_t>(sizeof(T) * tab.size());
+  PHI_CUDA_TRY(cudaMemcpyAsync(p.radial_tab, tab.data(), sizeof(T) * tab.size(),
+                               cudaMemcpyHostToDevice, s));
+  PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  return PHI_OK;
 }
 
 template <typename T, typename C>
@@ -999,7 +1256,19 @@ int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C
   const int64_t nk = p.stack_off[p.group_stacks[s1 - 1] + 1] - b0;
   if (nk == 0) return PHI_OK;
   const VisRec<T>* recs = static_cast<const VisRec<T>*>(p.recs) + b0;
-  if (p.d.kernel_mode == PHI_KERNEL_TABLE) {
+  if (p.d.kernel_mode == PHI_KERNEL_RADIAL) {
+    const size_t smem = radial_smem<T, C>(p);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vis_radial_kernel<T, C, kGrid>,
+                                                      kVisThreads, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    const int blocks = per_sm * p.num_sms;
+    vis_radial_kernel<T, C, kGrid><<<blocks, kVisThreads, smem, s>>>(
+        recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(),
+        radial_view<T, C>(p), p.stack_slot_dev, p.counters + g, p.counters + p.K,
+        queue_batch(nk, blocks * (kVisThreads / 32)));
+  } else if (p.d.kernel_mode == PHI_KERNEL_TABLE) {
     const int blocks = p.num_sms * 8;
     vis_table_kernel<T, C, kGrid><<<blocks, kVisThreads, 0, s>>>(
         recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, table_view<T, C>(p), p.npad,
@@ -1098,6 +1367,11 @@ int build_kernel_table(Plan& p, cudaStream_t s) {
   return build_table_t<float, float2>(p, s);
 }
 
+int build_radial_tables(Plan& p, cudaStream_t s) {
+  if (p.d.precision == PHI_F64) return build_radial_tables_t<double, double2>(p, s);
+  return build_radial_tables_t<float, float2>(p, s);
+}
+
 long timer_begin(Plan& p, cudaStream_t s) {
   if (!p.timing) return -1;
   size_t idx = 2 * p.ev_pending.size();
@@ -1135,6 +1409,19 @@ int set_kernel_smem_limits() {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f32));
   PHI_CUDA_TRY(cudaFuncSetAttribute(table_sample_kernel<double, double2>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f64));
+  // radial mode: its series storage depends on the plan; allow up to the
+  // device's opt-in limit (plans that would need more are refused)
+  int dev = 0, optin = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_radial_kernel<float, float2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_radial_kernel<float, float2, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_radial_kernel<double, double2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_radial_kernel<double, double2, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   return PHI_OK;
 }
 

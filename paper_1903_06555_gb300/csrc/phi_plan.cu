@@ -282,6 +282,7 @@ void free_plan(Plan* p) {
   cudaFree(p->node_hd);
   cudaFree(p->tap_order);
   cudaFree(p->tap_off);
+  cudaFree(p->radial_tab);
   cudaFree(p->grid);
   cudaFree(p->counters);
   cudaFree(p->table);
@@ -329,7 +330,9 @@ int validate(const phi_plan_desc& d, int64_t M) {
   if (d.max_refine < 0 || d.max_refine > 8) return PHI_ERR_ARG;
   if (d.tile < 0 || d.tile > 4096) return PHI_ERR_ARG;
   if (d.kb_beta < 0.0 || d.cycles_per_panel < 0.0) return PHI_ERR_ARG;
-  if (d.kernel_mode != PHI_KERNEL_QUADRATURE && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
+  if (d.kernel_mode != PHI_KERNEL_QUADRATURE && d.kernel_mode != PHI_KERNEL_TABLE &&
+      d.kernel_mode != PHI_KERNEL_RADIAL)
+    return PHI_ERR_ARG;
   if (d.grid_staging != 0 && d.grid_staging != 1) return PHI_ERR_ARG;
   if (d.max_grid_mib < 0 || d.reserved0 != 0) return PHI_ERR_ARG;
   if (d.grid_staging && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
@@ -687,6 +690,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
                              pair * (p.table_nw - 1) * p.table_nr));
     PHI_TRY(build_kernel_table(p, s));
   }
+  if (d.kernel_mode == PHI_KERNEL_RADIAL) PHI_TRY(build_radial_tables(p, s));
   if (cufftCreate(&p.fft) != CUFFT_SUCCESS) return PHI_ERR_CUDA;
   p.fft_ok = true;
   size_t work = 0;

@@ -101,7 +101,8 @@ def test_defaults_and_error_strings():
 BAD = [dict(image_n=127), dict(image_n=0), dict(support=3), dict(n_stacks=0),
        dict(n_stacks=200), dict(precision=5), dict(oversample=1.25), dict(fov_rad=-1.0),
        dict(max_support=2), dict(quad_rel_tol=0.0), dict(support_rule=3), dict(max_refine=-1),
-       dict(kernel_mode=2), dict(kernel_mode=1, table_tol=0.0), dict(grid_staging=2),
+       dict(kernel_mode=3), dict(kernel_mode=1, table_tol=0.0), dict(grid_staging=2),
+       dict(kernel_mode=2, grid_staging=1),
        dict(grid_staging=1), dict(max_grid_mib=-1), dict(reserved0=1)]
 
 
