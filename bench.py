@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=200)
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="offered load of the Poisson stream as a fraction of the measured capacity")
+    ap.add_argument("--serve-kernel-mode", default="quadrature", choices=["quadrature", "radial"],
+                    help="kernel mode of every request in the serving stream")
     ap.add_argument("--serve-full-scale", type=int, default=1,
                     help="append the 126.6M-visibility request to the serving stream")
     ap.add_argument("--support-rule", default="stack", choices=["stack", "vis"])
@@ -601,7 +603,7 @@ def run_e2e(phi, desc, uvw_np, x_np, steps, dev):
 # ---------------------------------------------------------------------------- serving
 
 def serve_requests(n, seed=0, mmin=5e4, mmax=2e7, sizes=(512, 1024, 2048, 4096, 8192),
-                   precision="f32", cap=64):
+                   precision="f32", cap=64, kernel_mode="quadrature"):
     """Synthetic serving stream: observations of log-uniform visibility
     counts, image sizes log-uniform over powers of two, |w|max ~ U[50, 3000]
     (fold on), K ~ U{1..64} raised by the client where the support would
@@ -622,7 +624,7 @@ def serve_requests(n, seed=0, mmin=5e4, mmax=2e7, sizes=(512, 1024, 2048, 4096, 
                                    float(n_times) / 240, n_times, wmax=wmax, seed=seed * 1000 + i)[:m]
         desc = dict(image_n=N, fov_rad=fov, n_stacks=k, conj_fold=1, precision=precision,
                     max_support=cap, quad_rel_tol=1e-12 if precision == "f64" else 1e-6,
-                    quad_abs_tol=1e-12 if precision == "f64" else 1e-6)
+                    quad_abs_tol=1e-12 if precision == "f64" else 1e-6, kernel_mode=kernel_mode)
         img = W.point_sources(N, 20, seed * 1000 + i)
         reqs.append(S.Request(i, np.ascontiguousarray(uvw), desc, image=img,
                               ops=("degrid", "grid")))
@@ -645,13 +647,14 @@ def run_serve(args):
     exceed the cap are retried by the engine with twice the stacks."""
     from paper_1903_06555_gb300 import serve as S
     budget = 150 * 10 ** 9
-    probe = serve_requests(24, seed=99)
+    km = args.serve_kernel_mode
+    probe = serve_requests(24, seed=99, kernel_mode=km)
     for r in probe:
         r.raise_stacks = True
     with S.Server(budget, slots=4) as srv:
         pres = srv.run_stream(probe, realtime=False)
     cap = S.summarize(pres, t_first=0.0)
-    reqs = serve_requests(args.serve_requests, seed=1)
+    reqs = serve_requests(args.serve_requests, seed=1, kernel_mode=km)
     for r in reqs:
         r.raise_stacks = True
     # offered load = arrival rate x mean kept visibilities per request of
@@ -667,7 +670,8 @@ def run_serve(args):
         uvw = W.uvw_earth_rotation(128, 3000.0, 150e6, -26.7, -37.2, -n_times / 240,
                                    n_times / 240, n_times, wmax=600.0, seed=5)[:126_600_000]
         full = Request(10_000, np.ascontiguousarray(uvw),
-                       dict(image_n=8192, fov_rad=math.radians(25.0), n_stacks=64, conj_fold=1),
+                       dict(image_n=8192, fov_rad=math.radians(25.0), n_stacks=64, conj_fold=1,
+                            kernel_mode=km),
                        image=W.point_sources(8192, 200, 5), ops=("degrid", "grid"),
                        arrival=reqs[len(reqs) // 2].arrival, raise_stacks=True)
         reqs.append(full)
@@ -692,7 +696,7 @@ def run_serve(args):
             "workload": "serving: Poisson stream of %d observations (5e4-2e7 vis, 512^2-8192^2, "
                         "|w|max 50-3000, K 1-64 raised to fit J_w <= 64) + 126.6M-vis 8192^2 request"
                         % args.serve_requests,
-            "capacity_closed_loop": cap, "offered_load": args.serve_load,
+            "kernel_mode": km, "capacity_closed_loop": cap, "offered_load": args.serve_load,
             "mean_kept_per_request": mean_kept, "arrival_rate_per_s": rate, "hbm_budget_bytes": budget,
             "peak_admitted_bytes": peak, "summary": summ, "stacks_raised": raised,
             "full_scale": None if not full_res else {
