@@ -406,6 +406,94 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
   }
 }
 
+// ---------------------------------------------------------------------------
+// Pieces shared by the per-visibility kernels
+// ---------------------------------------------------------------------------
+
+// A warp's share of the work queue: visibilities are claimed `batch` at a
+// time from the shared head (one atomic per batch).  take() is false once the
+// queue is empty.
+struct WarpQueue {
+  unsigned long long next = 0, stop = 0;
+  __device__ __forceinline__ bool take(unsigned long long* head, unsigned long long batch,
+                                       int64_t n, int lane, unsigned long long& i) {
+    if (next == stop) {
+      unsigned long long i0 = 0;
+      if (lane == 0) i0 = atomicAdd(head, batch);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+      next = i0;
+      stop = min(i0 + batch, static_cast<unsigned long long>(n));
+      if (next >= stop) return false;
+    }
+    i = next++;
+    return true;
+  }
+};
+
+// The value a gridded visibility spreads: W_i y_i, conjugated back if folded.
+template <typename T, typename C>
+__device__ __forceinline__ C load_visibility(const C* __restrict__ vis_in, uint32_t pm, T weight) {
+  C v = vis_in[pm & 0x7fffffffu];
+  if (pm >> 31) v.y = -v.y;
+  v.x *= weight;
+  v.y *= weight;
+  return v;
+}
+
+// One tap: gridding adds conj(K) yv to the grid cell, degridding accumulates
+// K times the cell.
+template <typename C, bool kGrid>
+__device__ __forceinline__ void apply_tap(const C& K, int64_t gi, const C& yv,
+                                          const C* __restrict__ grid_in, C* grid_out, C& accv) {
+  if (kGrid) {
+    C add;
+    add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
+    add.y = K.x * yv.y - K.y * yv.x;
+    atomic_add_c(grid_out + gi, add);
+  } else {
+    const C g = grid_in[gi];
+    accv.x += K.x * g.x - K.y * g.y;
+    accv.y += K.x * g.y + K.y * g.x;
+  }
+}
+
+// Degridding: the warp's tap sums reduced, weighted, conjugated if folded and
+// stored in the caller's order.
+template <typename T, typename C>
+__device__ __forceinline__ void store_visibility(C accv, T weight, uint32_t pm,
+                                                 C* __restrict__ vis_out, int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
+    accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
+  }
+  if (lane == 0) {
+    C out;
+    out.x = accv.x * weight;
+    out.y = accv.y * weight;
+    if (pm >> 31) out.y = -out.y;
+    vis_out[pm & 0x7fffffffu] = out;
+  }
+}
+
+// The warp's counters into the plan's statistics: [0] unconverged, [1] taps,
+// [3] tap-node evaluations.
+__device__ __forceinline__ void flush_counts(unsigned long long* stats, unsigned long long bad,
+                                             unsigned long long taps, unsigned long long nodes,
+                                             int lane) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    taps += __shfl_xor_sync(0xffffffffu, taps, o);
+    nodes += __shfl_xor_sync(0xffffffffu, nodes, o);
+  }
+  if (lane == 0 && taps) {
+    if (bad) atomicAdd(stats, bad);
+    atomicAdd(stats + 1, taps);
+    if (nodes) atomicAdd(stats + 3, nodes);
+  }
+}
+
 // Panels for the chunk: integrand cycles over [0, R] bounded by
 // R (rho_max + |dw| chirp_coeff), at inv_cycles panels per cycle.
 __device__ __forceinline__ int initial_panels(const QuadParams& q, float rho_max, float adw) {
@@ -430,20 +518,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
   NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int npad = q.npad;
-  // visibilities are claimed `batch` at a time (one atomic per batch on the
-  // shared queue head)
-  const unsigned long long kBatch = static_cast<unsigned long long>(batch);
-  unsigned long long next = 0, stop = 0;
-  while (true) {
-    if (next == stop) {
-      unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(head, kBatch);
-      i0 = __shfl_sync(0xffffffffu, i0, 0);
-      next = i0;
-      stop = min(i0 + kBatch, static_cast<unsigned long long>(n));
-      if (next >= stop) break;
-    }
-    const unsigned long long i = next++;
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
     // the grid of this visibility's stack within the resident group
@@ -454,13 +531,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
     const float adw = static_cast<float>(fabs(r.dw));
     int built = 0;
     const uint32_t pm = perm[i];
-    C yv = cmake<C>(0.0, 0.0);
-    if (kGrid) {
-      C v = vis_in[pm & 0x7fffffffu];
-      if (pm >> 31) v.y = -v.y;
-      yv.x = v.x * static_cast<T>(r.weight);
-      yv.y = v.y * static_cast<T>(r.weight);
-    }
+    const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                       : cmake<C>(0.0, 0.0);
     C accv = cmake<C>(0.0, 0.0);
     const int ntap = Jw * Jw;
     for (int t0 = 0; t0 < ntap; t0 += 32) {
@@ -482,44 +554,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
         if (!ok) ++my_bad;
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
-        if (kGrid) {
-          C add;
-          add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
-          add.y = K.x * yv.y - K.y * yv.x;
-          atomic_add_c(grid_out + gi, add);
-        } else {
-          const C g = grid_in[gi];
-          accv.x += K.x * g.x - K.y * g.y;
-          accv.y += K.x * g.y + K.y * g.x;
-        }
+        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
       }
     }
-    if (!kGrid) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
-        accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
-      }
-      if (lane == 0) {
-        C out;
-        out.x = accv.x * static_cast<T>(r.weight);
-        out.y = accv.y * static_cast<T>(r.weight);
-        if (pm >> 31) out.y = -out.y;
-        vis_out[pm & 0x7fffffffu] = out;
-      }
-    }
+    if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
-    my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
-    my_nodes += __shfl_xor_sync(0xffffffffu, my_nodes, o);
-  }
-  if (lane == 0 && my_taps) {
-    atomicAdd(stats, my_bad);
-    atomicAdd(stats + 1, my_taps);
-    atomicAdd(stats + 3, my_nodes);
-  }
+  flush_counts(stats, my_bad, my_taps, my_nodes, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -589,21 +629,11 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
   const int npad = npad_i;
   const int nr = static_cast<int>(tv.nr), nw = static_cast<int>(tv.nw);
   unsigned long long my_taps = 0;
-  // Visibilities are claimed `batch` at a time: with small supports a
-  // visibility is cheap and one atomic per visibility on the shared queue
-  // head would serialise the warps.
-  const unsigned long long kBatch = static_cast<unsigned long long>(batch);
-  unsigned long long next = 0, stop = 0;
-  while (true) {
-    if (next == stop) {
-      unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(head, kBatch);
-      i0 = __shfl_sync(0xffffffffu, i0, 0);
-      next = i0;
-      stop = min(i0 + kBatch, static_cast<unsigned long long>(n));
-      if (next >= stop) break;
-    }
-    const unsigned long long i = next++;
+  // batches of visibilities: with small supports a visibility is cheap and
+  // one atomic per visibility on the shared queue head would serialise warps
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
     // the grid of this visibility's stack within the resident group
@@ -618,13 +648,8 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
     const bool neg = r.dw < 0.0;
     const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
     const uint32_t pm = perm[i];
-    C yv = cmake<C>(0.0, 0.0);
-    if (kGrid) {
-      C v = vis_in[pm & 0x7fffffffu];
-      if (pm >> 31) v.y = -v.y;
-      yv.x = v.x * static_cast<T>(r.weight);
-      yv.y = v.y * static_cast<T>(r.weight);
-    }
+    const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                       : cmake<C>(0.0, 0.0);
     C accv = cmake<C>(0.0, 0.0);
     const int ntap = Jw * Jw;
     // Tap t = b Jw + a, advanced by 32 per chunk without a division per tap;
@@ -653,16 +678,7 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
         ++my_taps;
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
-        if (kGrid) {
-          C add;
-          add.x = K.x * yv.x + K.y * yv.y;
-          add.y = K.x * yv.y - K.y * yv.x;
-          atomic_add_c(grid_out + gi, add);
-        } else {
-          const C g = grid_in[gi];
-          accv.x += K.x * g.x - K.y * g.y;
-          accv.y += K.x * g.y + K.y * g.x;
-        }
+        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
       }
       a += step_a;
       b += step_b;
@@ -675,24 +691,9 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
         dv_ -= T(1);
       }
     }
-    if (!kGrid) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
-        accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
-      }
-      if (lane == 0) {
-        C out;
-        out.x = accv.x * static_cast<T>(r.weight);
-        out.y = accv.y * static_cast<T>(r.weight);
-        if (pm >> 31) out.y = -out.y;
-        vis_out[pm & 0x7fffffffu] = out;
-      }
-    }
+    if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
-  if (lane == 0 && my_taps) atomicAdd(stats + 1, my_taps);
+  flush_counts(stats, 0, my_taps, 0, lane);
 }
 
 // Degrid / grid with the tabulated kernel, one thread block per uv-tile work
@@ -753,13 +754,8 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
       const bool neg = r.dw < 0.0;
       const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
       const uint32_t pm = perm[ri];
-      C yv = cmake<C>(0.0, 0.0);
-      if (kGrid) {
-        C v = vis_in[pm & 0x7fffffffu];
-        if (pm >> 31) v.y = -v.y;
-        yv.x = v.x * static_cast<T>(r.weight);
-        yv.y = v.y * static_cast<T>(r.weight);
-      }
+      const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                         : cmake<C>(0.0, 0.0);
       // patch position of tap (0, 0) = (bu - half + 1, bv - half + 1)
       const int pu0 = r.bu - half + 1 - u0, pv0 = r.bv - half + 1 - v0;
       C accv = cmake<C>(0.0, 0.0);
@@ -804,20 +800,7 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
           dv_ -= T(1);
         }
       }
-      if (!kGrid) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
-          accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
-        }
-        if (lane == 0) {
-          C out;
-          out.x = accv.x * static_cast<T>(r.weight);
-          out.y = accv.y * static_cast<T>(r.weight);
-          if (pm >> 31) out.y = -out.y;
-          vis_out[pm & 0x7fffffffu] = out;
-        }
-      }
+      if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
     }
     __syncthreads();
     if (kGrid) {
@@ -833,9 +816,7 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
       __syncthreads();
     }
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
-  if (lane == 0 && my_taps) atomicAdd(stats + 1, my_taps);
+  flush_counts(stats, 0, my_taps, 0, lane);
 }
 
 // phi_wkernel: one warp per point, lane 0 carries the tap.
@@ -896,18 +877,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
   const int max_pieces = rv.buf / NS;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int npad = q.npad;
-  const unsigned long long kBatch = static_cast<unsigned long long>(batch);
-  unsigned long long next = 0, stop = 0;
-  while (true) {
-    if (next == stop) {
-      unsigned long long i0 = 0;
-      if (lane == 0) i0 = atomicAdd(head, kBatch);
-      i0 = __shfl_sync(0xffffffffu, i0, 0);
-      next = i0;
-      stop = min(i0 + kBatch, static_cast<unsigned long long>(n));
-      if (next >= stop) break;
-    }
-    const unsigned long long i = next++;
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
     const VisRec<T> r = recs[i];
     const int Jw = r.jw;
     const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
@@ -915,13 +887,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
     const T fu = r.fu, fv = r.fv;
     const float adw = static_cast<float>(fabs(r.dw));
     const uint32_t pm = perm[i];
-    C yv = cmake<C>(0.0, 0.0);
-    if (kGrid) {
-      C v = vis_in[pm & 0x7fffffffu];
-      if (pm >> 31) v.y = -v.y;
-      yv.x = v.x * static_cast<T>(r.weight);
-      yv.y = v.y * static_cast<T>(r.weight);
-    }
+    const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                       : cmake<C>(0.0, 0.0);
     // farthest tap: |u offset| <= max(half - fu, fu + half - 1), likewise in v;
     // the piece count is clamped to the storage the plan sized for its
     // largest support (a rounding excess is extrapolated by the last piece)
@@ -1024,16 +991,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
         ++my_taps;
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
-        if (kGrid) {
-          C add;
-          add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
-          add.y = K.x * yv.y - K.y * yv.x;
-          atomic_add_c(grid_out + gi, add);
-        } else {
-          const C g = grid_in[gi];
-          accv.x += K.x * g.x - K.y * g.y;
-          accv.y += K.x * g.y + K.y * g.x;
-        }
+        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
       }
       a += step_a;
       b += step_b;
@@ -1048,32 +1006,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
     }
     // the series storage is rewritten by the next visibility's samples
     __syncwarp();
-    if (!kGrid) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        accv.x += __shfl_xor_sync(0xffffffffu, accv.x, o);
-        accv.y += __shfl_xor_sync(0xffffffffu, accv.y, o);
-      }
-      if (lane == 0) {
-        C out;
-        out.x = accv.x * static_cast<T>(r.weight);
-        out.y = accv.y * static_cast<T>(r.weight);
-        if (pm >> 31) out.y = -out.y;
-        vis_out[pm & 0x7fffffffu] = out;
-      }
-    }
+    if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
-    my_taps += __shfl_xor_sync(0xffffffffu, my_taps, o);
-    my_nodes += __shfl_xor_sync(0xffffffffu, my_nodes, o);
-  }
-  if (lane == 0 && my_taps) {
-    atomicAdd(stats, my_bad);
-    atomicAdd(stats + 1, my_taps);
-    atomicAdd(stats + 3, my_nodes);
-  }
+  flush_counts(stats, my_bad, my_taps, my_nodes, lane);
 }
 
 // ---------------------------------------------------------------------------
