@@ -564,6 +564,81 @@ def grid(plan: OraclePlan, y, tol_rel=None, tol_abs=None, return_stats=False):
 
 
 # ----------------------------------------------------------------------------
+# Direction-dependent effects (Sec. 5.2)
+# ----------------------------------------------------------------------------
+#
+# A DDE model D_i in the uv domain, band-limited and given on the grid
+# (integer offsets s, |s_u|, |s_v| <= h, J_D = 2 h + 1 taps a side), enters by
+# a further convolution with the w-kernel: the combined kernel is
+# (D_i * [GC])(x) = sum_s D_i(s) [GC](x - s), so visibility i degrids with
+#     C_i(q) = sum_s D_i(s) [GC](|u_i/du - q - s|, dw_i)
+# on the J_w + J_D - 1 box around it, and grids with its conjugate.  D_i is
+# separable here, D_i(s) = a_i(s_u) b_i(s_v) (Sec. 5.2's cheaper case).  The
+# fold's conjugate symmetry (Sec. 3.3) only holds for DDEs that are real in
+# the image domain, so plans with folded visibilities are refused.
+
+
+def dde_taps(plan: OraclePlan, i, a, b, tol_rel=None, tol_abs=None):
+    """The combined taps C_i on the (J_w + J_D - 1)^2 box of visibility i,
+    rows v, columns u, and the box's first grid index (q0u - h, q0v - h)."""
+    geo = plan.geo
+    J = int(plan.jw[i])
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    h = (a.size - 1) // 2
+    q0u = int(np.floor(plan.upix[i])) - J // 2 + 1      # first tap, Sec. 2
+    q0v = int(np.floor(plan.vpix[i])) - J // 2 + 1
+    ku = plan.upix[i] - (q0u + np.arange(J))
+    kv = plan.vpix[i] - (q0v + np.arange(J))
+    rho = np.hypot(ku[None, :], kv[:, None]).ravel()
+    K = wkernel(rho, np.full(rho.size, plan.dw[i]), geo, tol_rel, tol_abs).reshape(J, J)
+    Jc = J + 2 * h
+    C = np.zeros((Jc, Jc), np.complex128)
+    # C[q] gets D(s) K[q + s - q0], i.e. K shifted by -s inside the larger box
+    for sv in range(-h, h + 1):
+        for su in range(-h, h + 1):
+            C[h - sv:h - sv + J, h - su:h - su + J] += a[su + h] * b[sv + h] * K
+    return C, q0u - h, q0v - h
+
+
+def degrid_dde(plan: OraclePlan, x, a, b, tol_rel=None, tol_abs=None):
+    """y_i = W_i sum_q C_i(q) Xhat_k[q mod Npad] with the DDE kernels a[i],
+    b[i] (J_D taps each, offsets -h..h)."""
+    if plan.flag.any():
+        raise ValueError("DDE convolution needs a plan without the conjugate fold")
+    geo = plan.geo
+    grids = stack_grids(plan, x)
+    y = np.zeros(plan.flag.size, np.complex128)
+    for i in np.nonzero(~plan.dropped)[0]:
+        C, cu, cv = dde_taps(plan, i, a[i], b[i], tol_rel, tol_abs)
+        n = C.shape[0]
+        rows = (cv + np.arange(n)) % geo.Npad
+        cols = (cu + np.arange(n)) % geo.Npad
+        g = grids[int(plan.stack[i])]
+        y[i] = plan.weight[i] * np.sum(C * g[np.ix_(rows, cols)])
+    return y
+
+
+def grid_dde(plan: OraclePlan, y, a, b, tol_rel=None, tol_abs=None):
+    """x = Re(Phi_D^H y): every visibility spreads conj(C_i) W_i y_i over its
+    box on its stack's grid; then as Phi^H."""
+    if plan.flag.any():
+        raise ValueError("DDE convolution needs a plan without the conjugate fold")
+    geo = plan.geo
+    grids = {}
+    for i in np.nonzero(~plan.dropped)[0]:
+        C, cu, cv = dde_taps(plan, i, a[i], b[i], tol_rel, tol_abs)
+        n = C.shape[0]
+        rows = (cv + np.arange(n)) % geo.Npad
+        cols = (cu + np.arange(n)) % geo.Npad
+        k = int(plan.stack[i])
+        if k not in grids:
+            grids[k] = np.zeros((geo.Npad, geo.Npad), np.complex128)
+        grids[k][np.ix_(rows, cols)] += np.conj(C) * (plan.weight[i] * y[i])
+    return image_from_grids(plan, grids)
+
+
+# ----------------------------------------------------------------------------
 # Pre-sampled 1-D w-planes (Sec. 5.1.1)
 # ----------------------------------------------------------------------------
 

@@ -450,3 +450,69 @@ def test_table_operator_close_to_direct_operator(table_case):
     lhs = np.real(np.vdot(yr, O.degrid_table(plan, xr, tab)))
     rhs = float(np.sum(xr * O.grid_table(plan, yr, tab)))
     assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+# ---------------------------------------------------------------- direction-dependent effects
+
+@pytest.fixture(scope="module")
+def dde_case():
+    geo = tiny_geo(tol_rel=1e-11, tol_abs=1e-11)
+    uvw = W.uvw_disk(40, 40.0, 30.0, 61)
+    plan = O.make_plan(uvw, geo, 2, False)
+    x = W.point_sources(128, 10, 61)
+    return geo, uvw, plan, x
+
+
+def test_dde_delta_is_the_plain_operator(dde_case):
+    """D = delta (J_D = 1): the combined kernel is the w-kernel (Sec. 5.2)."""
+    geo, uvw, plan, x = dde_case
+    n = len(uvw)
+    one = np.ones((n, 1), np.complex128)
+    assert O.rel_l2(O.degrid_dde(plan, x, one, one), O.degrid(plan, x)) < 1e-12
+    yr = W.random_vis(n, 62)
+    assert O.rel_l2(O.grid_dde(plan, yr, one, one), O.grid(plan, yr)) < 1e-12
+
+
+@pytest.mark.parametrize("su,sv", [(1, 0), (-2, 1), (0, -2)])
+def test_dde_shifted_delta_moves_the_visibility(dde_case, su, sv):
+    """D = delta at grid offset s: C(q) = [GC](u - s - q), i.e. the plain
+    operator for the visibility moved by -s pixels (same stacks and supports,
+    since w is unchanged)."""
+    geo, uvw, plan, x = dde_case
+    n, h = len(uvw), 2
+    a = np.zeros((n, 2 * h + 1), np.complex128)
+    b = np.zeros((n, 2 * h + 1), np.complex128)
+    a[:, su + h] = 1.0
+    b[:, sv + h] = 1.0
+    moved = uvw.copy()
+    moved[:, 0] -= su * geo.du
+    moved[:, 1] -= sv * geo.du
+    plan_m = O.make_plan(moved, geo, 2, False)
+    assert np.array_equal(plan_m.stack, plan.stack) and np.array_equal(plan_m.jw, plan.jw)
+    assert O.rel_l2(O.degrid_dde(plan, x, a, b), O.degrid(plan_m, x)) < 1e-12
+    yr = W.random_vis(n, 63)
+    assert O.rel_l2(O.grid_dde(plan, yr, a, b), O.grid(plan_m, yr)) < 1e-12
+
+
+def test_dde_adjoint_and_linearity(dde_case):
+    geo, uvw, plan, x = dde_case
+    n = len(uvw)
+    a, b = W.dde_kernels(n, 5, 64)
+    xr = W.random_image(128, 65)
+    yr = W.random_vis(n, 66)
+    y = O.degrid_dde(plan, xr, a, b)
+    lhs = np.real(np.vdot(yr, y))
+    rhs = np.sum(xr * O.grid_dde(plan, yr, a, b))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    c = 0.3 - 1.7j
+    assert O.rel_l2(O.degrid_dde(plan, xr, c * a, b), c * y) < 1e-13
+
+
+def test_dde_refuses_folded_plans():
+    geo = tiny_geo()
+    uvw = W.uvw_disk(10, 40.0, 30.0, 67)
+    plan = O.make_plan(uvw, geo, 1, True)
+    assert plan.flag.any()
+    one = np.ones((10, 1), np.complex128)
+    with pytest.raises(ValueError):
+        O.degrid_dde(plan, np.zeros((128, 128)), one, one)

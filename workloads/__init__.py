@@ -189,3 +189,24 @@ def subsample(m: int, k: int, seed: int = 0) -> np.ndarray:
     rng = np.random.default_rng(seed + 6000)
     k = min(k, m)
     return np.sort(rng.choice(m, size=k, replace=False))
+
+
+def dde_kernels(m: int, taps: int, seed: int = 0):
+    """Synthetic separable direction-dependent-effect kernels on the grid,
+    one pair per visibility: a[i] (u offsets -h..h) and b[i] (v offsets),
+    taps = 2 h + 1.  Each is a sampled Gaussian of width U[0.4, 1.2] pixels
+    centred U[-0.5, 0.5] pixels off, times a phase ramp of U[-0.5, 0.5] rad per
+    pixel (a smooth aperture-plane blur and shift, as a primary-beam or
+    ionospheric model would give), normalised to unit sum of magnitudes.
+    complex128 (m, taps) each."""
+    rng = np.random.default_rng(seed + 7000)
+    h = (taps - 1) // 2
+    s = np.arange(-h, h + 1, dtype=np.float64)
+
+    def one():
+        sig = rng.uniform(0.4, 1.2, (m, 1))
+        off = rng.uniform(-0.5, 0.5, (m, 1))
+        ramp = rng.uniform(-0.5, 0.5, (m, 1))
+        k = np.exp(-0.5 * ((s[None, :] - off) / sig) ** 2) * np.exp(1j * ramp * s[None, :])
+        return k / np.sum(np.abs(k), axis=1, keepdims=True)
+    return one(), one()
