@@ -258,6 +258,31 @@ int phi_degrid(phi_plan_t plan, const void* image_dev, void* vis_dev, void* stre
 int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, void* stream);
 
 /*
+ * phi_degrid / phi_grid with a direction-dependent effect per visibility
+ * (Sec. 5.2): a band-limited DDE kernel D_i given on the grid, separable as
+ * D_i(s_u, s_v) = a_i(s_u) b_i(s_v) for offsets -h..h (dde_taps = 2 h + 1,
+ * odd, 1..15), convolved with the w-kernel.  Visibility i then degrids with
+ *     C_i(q) = sum_s D_i(s) [GC](|u_i/du - q - s|, w_i - wbar_k)
+ * over the (J_w + dde_taps - 1)^2 box around it and grids with conj(C_i).
+ * The w-kernel taps are integrated by the per-tap quadrature whatever the
+ * plan's kernel_mode.  dde_taps = 1 with a = b = 1 is phi_degrid / phi_grid.
+ *   dde_a_dev, dde_b_dev: n_vis x dde_taps complex of the plan's precision
+ *              (interleaved re, im), row-major, caller's visibility order;
+ *              entry j of a row is offset j - h.  Read only; the caller owns
+ *              them.
+ * The fold's conjugate symmetry (Sec. 3.3) holds only for DDEs that are real
+ * in the image domain, so a plan built with conj_fold = 1 gives PHI_ERR_ARG,
+ * as do dde_taps outside 1..15 or even, and NULL kernels with n_vis > 0.
+ * PHI_ERR_SUPPORT if one warp's w-kernel box for the plan's largest support
+ * does not fit in a thread block's shared memory.  No counterpart for the
+ * kernels' values: the paper gives no DDE model; they are the caller's.
+ */
+int phi_degrid_dde(phi_plan_t plan, const void* image_dev, const void* dde_a_dev,
+                   const void* dde_b_dev, int32_t dde_taps, void* vis_dev, void* stream);
+int phi_grid_dde(phi_plan_t plan, const void* vis_dev, const void* dde_a_dev,
+                 const void* dde_b_dev, int32_t dde_taps, void* image_dev, void* stream);
+
+/*
  * Evaluate [GC](rho_i, dw_i) (Eq. analytic_convolution_hankel) for n points
  * with the plan's geometry, taper and quadrature, by the same device routine
  * the degridder and gridder use.

@@ -601,32 +601,35 @@ def dde_taps(plan: OraclePlan, i, a, b, tol_rel=None, tol_abs=None):
     return C, q0u - h, q0v - h
 
 
-def degrid_dde(plan: OraclePlan, x, a, b, tol_rel=None, tol_abs=None):
+def degrid_dde(plan: OraclePlan, x, a, b, tol_rel=None, tol_abs=None, subset=None):
     """y_i = W_i sum_q C_i(q) Xhat_k[q mod Npad] with the DDE kernels a[i],
-    b[i] (J_D taps each, offsets -h..h)."""
+    b[i] (J_D taps each, offsets -h..h); for the visibilities in `subset`
+    only (caller order kept) when given."""
     if plan.flag.any():
         raise ValueError("DDE convolution needs a plan without the conjugate fold")
     geo = plan.geo
-    grids = stack_grids(plan, x)
+    sel = np.arange(plan.flag.size) if subset is None else np.asarray(subset)
+    grids = stack_grids(plan, x, sorted(set(int(k) for k in plan.stack[sel])))
     y = np.zeros(plan.flag.size, np.complex128)
-    for i in np.nonzero(~plan.dropped)[0]:
+    for i in sel[~plan.dropped[sel]]:
         C, cu, cv = dde_taps(plan, i, a[i], b[i], tol_rel, tol_abs)
         n = C.shape[0]
         rows = (cv + np.arange(n)) % geo.Npad
         cols = (cu + np.arange(n)) % geo.Npad
         g = grids[int(plan.stack[i])]
         y[i] = plan.weight[i] * np.sum(C * g[np.ix_(rows, cols)])
-    return y
+    return y if subset is None else y[sel]
 
 
-def grid_dde(plan: OraclePlan, y, a, b, tol_rel=None, tol_abs=None):
-    """x = Re(Phi_D^H y): every visibility spreads conj(C_i) W_i y_i over its
-    box on its stack's grid; then as Phi^H."""
+def grid_dde(plan: OraclePlan, y, a, b, tol_rel=None, tol_abs=None, subset=None):
+    """x = Re(Phi_D^H y): every visibility (of `subset`, when given) spreads
+    conj(C_i) W_i y_i over its box on its stack's grid; then as Phi^H."""
     if plan.flag.any():
         raise ValueError("DDE convolution needs a plan without the conjugate fold")
     geo = plan.geo
+    sel = np.arange(plan.flag.size) if subset is None else np.asarray(subset)
     grids = {}
-    for i in np.nonzero(~plan.dropped)[0]:
+    for i in sel[~plan.dropped[sel]]:
         C, cu, cv = dde_taps(plan, i, a[i], b[i], tol_rel, tol_abs)
         n = C.shape[0]
         rows = (cv + np.arange(n)) % geo.Npad

@@ -144,6 +144,8 @@ def lib():
                                            ctypes.POINTER(_i64), ctypes.c_int, _vp]
             L.phi_degrid.argtypes = [_vp, _vp, _vp, _vp]
             L.phi_grid.argtypes = [_vp, _vp, _vp, _vp]
+            L.phi_degrid_dde.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp]
+            L.phi_grid_dde.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int32, _vp, _vp]
             L.phi_wkernel.argtypes = [_vp, _vp, _vp, _i64, _vp, ctypes.POINTER(_i64), _vp]
             L.phi_wkernel_noalloc.argtypes = [ctypes.POINTER(WKernelParams), _vp, _vp, _i64, _vp,
                                               ctypes.POINTER(_i64), _vp]
@@ -282,6 +284,41 @@ class Plan:
             else self._image(out)
         _check(lib().phi_grid(self._h, ctypes.c_void_p(y.data_ptr()),
                               ctypes.c_void_p(x.data_ptr()), _stream(stream)), "phi_grid")
+        return x
+
+    def _dde(self, a, b):
+        a = torch.as_tensor(a)
+        b = torch.as_tensor(b)
+        if a.dim() != 2 or a.shape != b.shape or a.shape[0] != self.n_vis:
+            raise ValueError(f"DDE kernels must both be ({self.n_vis}, taps)")
+        return (a.to(self.device, self.complex_dtype).contiguous(),
+                b.to(self.device, self.complex_dtype).contiguous())
+
+    def degrid_dde(self, x, a, b, out=None, stream=None):
+        """y = Phi_D x with the per-visibility separable DDE kernels a, b
+        ((n_vis, taps) complex, taps odd; Sec. 5.2) convolved with the
+        w-kernel.  The plan must be built without the conjugate fold."""
+        x = self._image(x)
+        a, b = self._dde(a, b)
+        y = torch.empty(self.n_vis, dtype=self.complex_dtype, device=self.device) if out is None \
+            else self._vis(out)
+        _check(lib().phi_degrid_dde(self._h, ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                    a.shape[1], ctypes.c_void_p(y.data_ptr()), _stream(stream)),
+               "phi_degrid_dde")
+        return y
+
+    def grid_dde(self, y, a, b, out=None, stream=None):
+        """x = Re(Phi_D^H y), the adjoint of degrid_dde."""
+        y = self._vis(y)
+        a, b = self._dde(a, b)
+        n = self.image_n
+        x = torch.empty((n, n), dtype=self.real_dtype, device=self.device) if out is None \
+            else self._image(out)
+        _check(lib().phi_grid_dde(self._h, ctypes.c_void_p(y.data_ptr()),
+                                  ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                  a.shape[1], ctypes.c_void_p(x.data_ptr()), _stream(stream)),
+               "phi_grid_dde")
         return x
 
     def wkernel(self, rho, dw, stream=None):

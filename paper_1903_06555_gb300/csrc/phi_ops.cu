@@ -1012,6 +1012,108 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
 }
 
 // ---------------------------------------------------------------------------
+// Direction-dependent effects (Sec. 5.2)
+// ---------------------------------------------------------------------------
+
+// Degrid / grid with a separable DDE kernel D_i(s) = a_i(s_u) b_i(s_v)
+// (J_D = 2 h + 1 taps a side, caller's visibility order) convolved with the
+// w-kernel: the warp integrates the visibility's J_w x J_w w-kernel taps by
+// the per-tap quadrature into shared memory, then forms every tap of the
+// (J_w + J_D - 1)^2 box as C(q) = sum_s D(s) [GC](u - q - s), i.e. from the
+// stored taps K[q + s - q0].
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
+    const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
+    const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
+    C* __restrict__ vis_out, QuadParams q, const C* __restrict__ dde_a,
+    const C* __restrict__ dde_b, int jd, int box_max, const int32_t* __restrict__ stack_slot,
+    unsigned long long* head, unsigned long long* stats, int batch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
+  C* box = reinterpret_cast<C*>(smem_raw + (blockDim.x >> 5) * kNodeBatch * sizeof(NodeVal<T>)) +
+           warp * (box_max * box_max + 2 * jd);
+  C* dab = box + box_max * box_max;   // a_i then b_i
+  const int h = jd >> 1;
+  unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
+  const int npad = q.npad;
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw;
+    const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
+    const int half = Jw / 2;
+    const T fu = r.fu, fv = r.fv;
+    const uint16_t* order = q.tap_order + q.tap_off[half - 1];
+    const float adw = static_cast<float>(fabs(r.dw));
+    int built = 0;
+    const uint32_t pm = perm[i];
+    const int64_t src = pm & 0x7fffffffu;
+    const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                       : cmake<C>(0.0, 0.0);
+    if (lane < 2 * jd) dab[lane] = lane < jd ? dde_a[src * jd + lane] : dde_b[src * jd + lane - jd];
+    // 1. the w-kernel on the J_w box, by the per-tap quadrature (ring order)
+    const int ntap = Jw * Jw;
+    for (int t0 = 0; t0 < ntap; t0 += 32) {
+      const int t = t0 + lane;
+      const bool active = t < ntap;
+      const uint32_t code = order[active ? t : 0];
+      const int ka = static_cast<int>(code & 0xffu), kb = static_cast<int>(code >> 8);
+      const T du_ = fu - static_cast<T>(ka - half + 1), dv_ = fv - static_cast<T>(kb - half + 1);
+      const T rho = sqrt(du_ * du_ + dv_ * dv_);
+      T rmax = active ? rho : T(0);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      const int npan = initial_panels(q, static_cast<float>(rmax), adw);
+      bool ok = true;
+      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, built, ok, lane, my_nodes);
+      if (active) {
+        box[kb * Jw + ka] = K;
+        if (!ok) ++my_bad;
+      }
+    }
+    __syncwarp();
+    // 2. the combined taps, raster order over the J_w + 2 h box
+    C accv = cmake<C>(0.0, 0.0);
+    const int Jc = Jw + 2 * h, nc = Jc * Jc;
+    for (int c0 = 0; c0 < nc; c0 += 32) {
+      const int c = c0 + lane;
+      if (c < nc) {
+        const int cv = c / Jc, cu = c - cv * Jc;
+        C acc = cmake<C>(0.0, 0.0);
+        for (int sv = -h; sv <= h; ++sv) {
+          const int kb = cv - h + sv;
+          if (kb < 0 || kb >= Jw) continue;
+          C row = cmake<C>(0.0, 0.0);
+          for (int su = -h; su <= h; ++su) {
+            const int ka = cu - h + su;
+            if (ka < 0 || ka >= Jw) continue;
+            const C kv = box[kb * Jw + ka];
+            const C av = dab[su + h];
+            row.x += av.x * kv.x - av.y * kv.y;
+            row.y += av.x * kv.y + av.y * kv.x;
+          }
+          const C bv = dab[jd + sv + h];
+          acc.x += bv.x * row.x - bv.y * row.y;
+          acc.y += bv.x * row.y + bv.y * row.x;
+        }
+        ++my_taps;
+        const int ou = cu - h - half + 1, ov = cv - h - half + 1;
+        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                           wrap_index(r.bu + ou, npad);
+        apply_tap<C, kGrid>(acc, gi, yv, grid_in, grid_out, accv);
+      }
+    }
+    // the box and the DDE taps are rewritten for the next visibility
+    __syncwarp();
+    if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
+  }
+  flush_counts(stats, my_bad, my_taps, my_nodes, lane);
+}
+
+// ---------------------------------------------------------------------------
 // Host side of the operator
 // ---------------------------------------------------------------------------
 namespace {
@@ -1177,10 +1279,56 @@ int fft_group(Plan& p, C* grids, int n, int dir, cudaStream_t s) {
 
 // The fused kernel over all records of the group's stacks (contiguous in
 // the sorted order).
+// Per-visibility separable DDE kernels of phi_degrid_dde / phi_grid_dde.
+struct DdeArgs {
+  const void* a;
+  const void* b;
+  int jd;
+};
+
+// Shared memory of one warp of vis_dde_kernel: the quadrature nodes, the
+// w-kernel box of the plan's largest support and the two DDE kernels.
+template <typename T, typename C>
+size_t dde_warp_smem(const Plan& p, int jd) {
+  const size_t jmax = static_cast<size_t>(std::max(p.max_jw, 2));
+  return kNodeBatch * sizeof(NodeVal<T>) + (jmax * jmax + 2 * jd) * sizeof(C);
+}
+
+template <typename T, typename C, bool kGrid>
+int launch_dde(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, int g, const C* grids_in,
+               C* grids_out, const C* vis_in, C* vis_out, const DdeArgs& dde, cudaStream_t s) {
+  int dev = 0, optin = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  const size_t per_warp = dde_warp_smem<T, C>(p, dde.jd);
+  const int warps = static_cast<int>(std::min<size_t>(kVisThreads / 32, optin / per_warp));
+  if (warps < 1) return PHI_ERR_SUPPORT;
+  const size_t smem = per_warp * warps;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vis_dde_kernel<T, C, kGrid>,
+                                                    32 * warps, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int blocks = per_sm * p.num_sms;
+  vis_dde_kernel<T, C, kGrid><<<blocks, 32 * warps, smem, s>>>(
+      recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(),
+      static_cast<const C*>(dde.a), static_cast<const C*>(dde.b), dde.jd, std::max(p.max_jw, 2),
+      p.stack_slot_dev, p.counters + g, p.counters + p.K, queue_batch(nk, blocks * warps));
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
 template <typename T, typename C, bool kGrid>
 int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C* vis_in,
-                        C* vis_out, cudaStream_t s) {
+                        C* vis_out, cudaStream_t s, const DdeArgs* dde = nullptr) {
   const int64_t s0 = p.group_off[g], s1 = p.group_off[g + 1];
+  if (dde) {
+    const int64_t b0 = p.stack_off[p.group_stacks[s0]];
+    const int64_t nk = p.stack_off[p.group_stacks[s1 - 1] + 1] - b0;
+    if (nk == 0) return PHI_OK;
+    return launch_dde<T, C, kGrid>(p, static_cast<const VisRec<T>*>(p.recs) + b0, b0, nk, g,
+                                   grids_in, grids_out, vis_in, vis_out, *dde, s);
+  }
   if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.d.grid_staging) {
     for (int64_t i = s0; i < s1; ++i)
       PHI_TRY_ST((launch_tile_table<T, C, kGrid>(p, p.group_stacks[i], grids_in, grids_out, vis_in,
@@ -1221,7 +1369,7 @@ int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C
 }
 
 template <typename T, typename C>
-int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
+int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s, const DdeArgs* dde = nullptr) {
   long ev = timer_begin(p, s);
   PHI_CUDA_TRY(cudaMemsetAsync(y, 0, sizeof(C) * (size_t)p.M, s));
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
@@ -1240,14 +1388,14 @@ int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s) {
     PHI_TRY_ST((fft_group<T, C>(p, grids, n, CUFFT_FORWARD, s)));
     timer_end(p, ev, PHI_STAGE_FFT, s);
     ev = timer_begin(p, s);
-    PHI_TRY_ST((launch_group_kernel<T, C, false>(p, g, grids, nullptr, nullptr, y, s)));
+    PHI_TRY_ST((launch_group_kernel<T, C, false>(p, g, grids, nullptr, nullptr, y, s, dde)));
     timer_end(p, ev, PHI_STAGE_DEGRID, s);
   }
   return PHI_OK;
 }
 
 template <typename T, typename C>
-int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
+int run_grid(Plan& p, const C* y, T* x, cudaStream_t s, const DdeArgs* dde = nullptr) {
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
   C* grids = static_cast<C*>(p.grid);
   const int64_t plane = static_cast<int64_t>(p.npad) * p.npad;
@@ -1258,7 +1406,7 @@ int run_grid(Plan& p, const C* y, T* x, cudaStream_t s) {
     PHI_CUDA_TRY(cudaMemsetAsync(grids, 0, sizeof(C) * plane * n, s));
     timer_end(p, ev, PHI_STAGE_CLEAR, s);
     ev = timer_begin(p, s);
-    PHI_TRY_ST((launch_group_kernel<T, C, true>(p, g, nullptr, grids, y, nullptr, s)));
+    PHI_TRY_ST((launch_group_kernel<T, C, true>(p, g, nullptr, grids, y, nullptr, s, dde)));
     timer_end(p, ev, PHI_STAGE_GRID, s);
     ev = timer_begin(p, s);
     PHI_TRY_ST((fft_group<T, C>(p, grids, n, CUFFT_INVERSE, s)));
@@ -1357,6 +1505,14 @@ int set_kernel_smem_limits() {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   PHI_CUDA_TRY(cudaFuncSetAttribute(vis_radial_kernel<double, double2, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<float, float2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<float, float2, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<double, double2, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<double, double2, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   return PHI_OK;
 }
 
@@ -1383,6 +1539,48 @@ extern "C" int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, v
                                           static_cast<double*>(image_dev), s);
   return phi::run_grid<float, float2>(p, static_cast<const float2*>(vis_dev),
                                       static_cast<float*>(image_dev), s);
+}
+
+namespace {
+int dde_check(phi_plan_t plan, const void* a, const void* b, int32_t taps) {
+  if (!plan || taps < 1 || taps > 15 || taps % 2 == 0) return PHI_ERR_ARG;
+  if (plan->M > 0 && (!a || !b)) return PHI_ERR_ARG;
+  if (plan->d.conj_fold) return PHI_ERR_ARG;
+  return PHI_OK;
+}
+}  // namespace
+
+extern "C" int phi_degrid_dde(phi_plan_t plan, const void* image_dev, const void* dde_a_dev,
+                              const void* dde_b_dev, int32_t dde_taps, void* vis_dev,
+                              void* stream) {
+  const int st = dde_check(plan, dde_a_dev, dde_b_dev, dde_taps);
+  if (st != PHI_OK) return st;
+  if ((!image_dev || !vis_dev) && plan->M > 0) return PHI_ERR_ARG;
+  phi::Plan& p = *plan;
+  if (p.M == 0) return PHI_OK;
+  const phi::DdeArgs dde{dde_a_dev, dde_b_dev, dde_taps};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.d.precision == PHI_F64)
+    return phi::run_degrid<double, double2>(p, static_cast<const double*>(image_dev),
+                                            static_cast<double2*>(vis_dev), s, &dde);
+  return phi::run_degrid<float, float2>(p, static_cast<const float*>(image_dev),
+                                        static_cast<float2*>(vis_dev), s, &dde);
+}
+
+extern "C" int phi_grid_dde(phi_plan_t plan, const void* vis_dev, const void* dde_a_dev,
+                            const void* dde_b_dev, int32_t dde_taps, void* image_dev,
+                            void* stream) {
+  const int st = dde_check(plan, dde_a_dev, dde_b_dev, dde_taps);
+  if (st != PHI_OK) return st;
+  if (!image_dev || (!vis_dev && plan->M > 0)) return PHI_ERR_ARG;
+  phi::Plan& p = *plan;
+  const phi::DdeArgs dde{dde_a_dev, dde_b_dev, dde_taps};
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (p.d.precision == PHI_F64)
+    return phi::run_grid<double, double2>(p, static_cast<const double2*>(vis_dev),
+                                          static_cast<double*>(image_dev), s, &dde);
+  return phi::run_grid<float, float2>(p, static_cast<const float2*>(vis_dev),
+                                      static_cast<float*>(image_dev), s, &dde);
 }
 
 extern "C" int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, int64_t n,

@@ -130,6 +130,8 @@ def test_null_handles_rejected():
     assert L.phi_degrid(None, None, None, None) == phi.PHI_ERR_ARG
     assert L.phi_grid(None, None, None, None) == phi.PHI_ERR_ARG
     assert L.phi_wkernel(None, None, None, 0, None, None, None) == phi.PHI_ERR_ARG
+    assert L.phi_degrid_dde(None, None, None, None, 5, None, None) == phi.PHI_ERR_ARG
+    assert L.phi_grid_dde(None, None, None, None, 5, None, None) == phi.PHI_ERR_ARG
     assert L.phi_plan_info(None, None, None, None, None) == phi.PHI_ERR_ARG
     L.phi_plan_destroy(None)
 
