@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="mwa", choices=["mwa", "serve", "plan", "precision", "diff"],
+    ap.add_argument("--workload", default="mwa",
+                    choices=["mwa", "serve", "plan", "precision", "diff", "dde"],
                     help="mwa: the headline operator benchmark; serve: the serving stream; "
                          "plan: Algorithm 1 and the fold at the paper's scale")
     ap.add_argument("--serve-requests", type=int, default=200)
@@ -938,6 +939,52 @@ def run_diff(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dde(args):
+    """Direction-dependent effects (Sec. 5.2): the MWA-like snapshot without
+    the fold (16 stacks), a synthetic separable DDE kernel of 5 x 5 taps per
+    visibility convolved with the w-kernel; degrid + grid timed against the
+    plain operator on the same plan."""
+    import paper_1903_06555_gb300 as phi
+    dev = torch.device("cuda", torch.cuda.current_device())
+    wl = W.mwa_snapshot()
+    uvw_np, x_np = workload_inputs(wl)
+    jd = 5
+    a_np, b_np = W.dde_kernels(len(uvw_np), jd, 77)
+    plan = phi.Plan(torch.from_numpy(uvw_np).to(dev), image_n=wl.image_n,
+                    fov_rad=math.radians(wl.fov_deg), n_stacks=16, conj_fold=0)
+    info = plan.info()
+    x = torch.from_numpy(x_np).to(dev, torch.float32)
+    y = torch.from_numpy(W.random_vis(len(uvw_np), 4)).to(dev, torch.complex64)
+    a = torch.from_numpy(a_np).to(dev, torch.complex64)
+    b = torch.from_numpy(b_np).to(dev, torch.complex64)
+    ms_plain = timed_ms(lambda: (plan.degrid(x), plan.grid(y)), args.steps, args.warmup)
+    plan.stats_full(reset=True)
+    ms_dde = timed_ms(lambda: (plan.degrid_dde(x, a, b), plan.grid_dde(y, a, b)), args.steps,
+                      args.warmup)
+    bad, taps, nodes = plan.stats_full(reset=True)
+    calls = 2 * (args.steps + args.warmup)
+    n_kept = info["n_kept"]
+    # executed work: the quadrature tap-nodes of the w-kernel boxes and, per
+    # combined tap, (J_D^2 + J_D) complex multiply-adds of 8 flops
+    flops = (nodes * FLOPS_PER_TAP_NODE + taps * (jd * jd + jd) * 8.0) / calls
+    ach = flops / (ms_dde / 2 / 1e3) / 1e12
+    peaks = measured_peaks()
+    peak_fp32 = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    line = {"metric": "w-corrected visibilities/s with a DDE per visibility (degrid+grid)",
+            "value": n_kept / (ms_dde / 1e3), "unit": UNIT,
+            "workload": f"{wl.name} without the fold: 16 stacks (J_w up to {info['max_jw']}), "
+                        f"{n_kept} kept visibilities, separable {jd}x{jd} DDE kernels",
+            "ms_per_step": ms_dde, "plain_operator_ms_per_step": ms_plain,
+            "plain_operator_vis_per_s": n_kept / (ms_plain / 1e3),
+            "combined_taps_per_vis": taps / calls / n_kept,
+            "quadrature_tap_nodes_per_vis": nodes / calls / n_kept, "unconverged": bad,
+            "roofline": {"bound": "alu", "kernel": "vis_dde_kernel", "achieved": ach,
+                         "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32,
+                         "work_note": "executed work: 36 flops per quadrature tap-node + "
+                                      "(J_D^2 + J_D) complex multiply-adds per combined tap"}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup(args)
@@ -955,6 +1002,9 @@ def main():
     elif args.workload == "diff":
         if rank == 0:
             run_diff(args)
+    elif args.workload == "dde":
+        if rank == 0:
+            run_dde(args)
     else:
         run_ours(args, ws, rank, local)
     if ws > 1:

@@ -1297,11 +1297,25 @@ size_t dde_warp_smem(const Plan& p, int jd) {
 template <typename T, typename C, bool kGrid>
 int launch_dde(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, int g, const C* grids_in,
                C* grids_out, const C* vis_in, C* vis_out, const DdeArgs& dde, cudaStream_t s) {
-  int dev = 0, optin = 0;
+  int dev = 0, optin = 0, per_sm_smem = 0, reserved = 0;
   PHI_CUDA_TRY(cudaGetDevice(&dev));
   PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                      dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
+  // warps per block that keep the most warps resident per SM (the boxes are
+  // large: a block of 8 can leave most of an SM's shared memory unused)
   const size_t per_warp = dde_warp_smem<T, C>(p, dde.jd);
-  const int warps = static_cast<int>(std::min<size_t>(kVisThreads / 32, optin / per_warp));
+  int warps = 0, best = 0;
+  for (int w = 1; w <= kVisThreads / 32; ++w) {
+    const size_t blk = per_warp * w;
+    if (blk > static_cast<size_t>(optin)) break;
+    const int resident = w * static_cast<int>(per_sm_smem / (blk + reserved));
+    if (resident >= best) {
+      best = resident;
+      warps = w;
+    }
+  }
   if (warps < 1) return PHI_ERR_SUPPORT;
   const size_t smem = per_warp * warps;
   int per_sm = 0;
