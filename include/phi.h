@@ -15,7 +15,12 @@
  *                              J0(2 pi rho r) r dr          (Eq. analytic_convolution_hankel)
  *
  * is computed on the fly by adaptive Gauss-Kronrod quadrature inside the
- * degridding and gridding kernels; no kernel table and no sparse G is stored.
+ * degridding and gridding kernels (PHI_KERNEL_QUADRATURE, the default); no
+ * sparse G is ever stored.  Alternatives: pre-sampled 1-D w-planes with
+ * bilinear interpolation (PHI_KERNEL_TABLE, Sec. 5.1.1), and a per-visibility
+ * Chebyshev series in rho built from the same quadrature (PHI_KERNEL_RADIAL).
+ * phi_degrid_dde / phi_grid_dde add a direction-dependent-effect kernel per
+ * visibility by a further convolution (Sec. 5.2).
  *
  * Conventions shared by every call:
  *   - Pixels: l_j = (j - N/2) * dl, dl = fov_rad / N, for row (m) and column
@@ -68,7 +73,9 @@ enum phi_status {
   PHI_ERR_OOM = 2,      /* device allocation failed                          */
   PHI_ERR_CUDA = 3,     /* a CUDA runtime or cuFFT call failed               */
   PHI_ERR_HORIZON = 4,  /* image or kernel window reaches l^2 + m^2 >= 1      */
-  PHI_ERR_SUPPORT = 5,  /* a stack needs J_w > max_support (raise K or cap)   */
+  PHI_ERR_SUPPORT = 5,  /* a stack needs J_w > max_support (raise K or cap),
+                           or the radial / DDE per-warp storage for the largest
+                           support exceeds a thread block's shared memory    */
   PHI_ERR_TIMEOUT = 6,  /* a bounded wait ran out                            */
   PHI_ERR_STATE = 7     /* the call does not apply to this plan              */
 };
