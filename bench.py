@@ -964,6 +964,21 @@ def run_dde(args):
     bad, taps, nodes = plan.stats_full(reset=True)
     calls = 2 * (args.steps + args.warmup)
     n_kept = info["n_kept"]
+    yq = plan.degrid_dde(x, a, b)
+    plan.close()
+    # the same with the w-kernel box filled from the radial mode's series
+    rplan = phi.Plan(torch.from_numpy(uvw_np).to(dev), image_n=wl.image_n,
+                     fov_rad=math.radians(wl.fov_deg), n_stacks=16, conj_fold=0,
+                     kernel_mode="radial")
+    ms_rdde = timed_ms(lambda: (rplan.degrid_dde(x, a, b), rplan.grid_dde(y, a, b)), args.steps,
+                       args.warmup)
+    ms_rplain = timed_ms(lambda: (rplan.degrid(x), rplan.grid(y)), args.steps, args.warmup)
+    yr = rplan.degrid_dde(x, a, b)
+    radial = {"vis_per_s": n_kept / (ms_rdde / 1e3), "ms_per_step": ms_rdde,
+              "plain_operator_ms_per_step": ms_rplain,
+              "rel_l2_vs_quadrature_box": float(torch.linalg.vector_norm(yr - yq) /
+                                                torch.linalg.vector_norm(yq))}
+    rplan.close()
     # executed work: the quadrature tap-nodes of the w-kernel boxes and, per
     # combined tap, (J_D^2 + J_D) complex multiply-adds of 8 flops
     flops = (nodes * FLOPS_PER_TAP_NODE + taps * (jd * jd + jd) * 8.0) / calls
@@ -978,6 +993,7 @@ def run_dde(args):
             "plain_operator_vis_per_s": n_kept / (ms_plain / 1e3),
             "combined_taps_per_vis": taps / calls / n_kept,
             "quadrature_tap_nodes_per_vis": nodes / calls / n_kept, "unconverged": bad,
+            "radial_mode": radial,
             "roofline": {"bound": "alu", "kernel": "vis_dde_kernel", "achieved": ach,
                          "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32,
                          "work_note": "executed work: 36 flops per quadrature tap-node + "

@@ -271,8 +271,10 @@ int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, void* stream
  * odd, 1..15), convolved with the w-kernel.  Visibility i then degrids with
  *     C_i(q) = sum_s D_i(s) [GC](|u_i/du - q - s|, w_i - wbar_k)
  * over the (J_w + dde_taps - 1)^2 box around it and grids with conj(C_i).
- * The w-kernel taps are integrated by the per-tap quadrature whatever the
- * plan's kernel_mode.  dde_taps = 1 with a = b = 1 is phi_degrid / phi_grid.
+ * The w-kernel taps come from the per-tap quadrature, or from the
+ * per-visibility Chebyshev series in a PHI_KERNEL_RADIAL plan (a
+ * PHI_KERNEL_TABLE plan also integrates them per tap).  dde_taps = 1 with
+ * a = b = 1 is phi_degrid / phi_grid.
  *   dde_a_dev, dde_b_dev: n_vis x dde_taps complex of the plan's precision
  *              (interleaved re, im), row-major, caller's visibility order;
  *              entry j of a row is offset j - h.  Read only; the caller owns

@@ -852,12 +852,118 @@ __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__
 // ---------------------------------------------------------------------------
 
 // For one visibility, [GC](., dw) is an even function of rho band-limited to
-// R cycles per grid pixel (the integral runs over r <= R).  The warp
+// R cycles per grid pixel (the integral runs over r <= R).  radial_series
 // integrates it by eval_chunk's quadrature at the Chebyshev points of pieces
-// of [0, rho_max] of width L = 2 / R, turns each piece's values into its
-// Chebyshev coefficients in shared memory (in place), and evaluates every tap
-// from its piece's series by Clenshaw's recurrence.  A piece whose two
-// trailing coefficients exceed the tolerance is counted as unconverged.
+// of [0, rho_max] of width L = 2 / R, and turns each piece's values into its
+// Chebyshev coefficients in `ser` (in place); a piece whose two trailing
+// coefficients exceed the tolerance is counted as unconverged.  radial_eval
+// then gives the kernel at any rho <= rho_max by Clenshaw's recurrence.
+template <typename T, typename C>
+__device__ __forceinline__ int radial_series(C* ser, NodeVal<T>* sh, const QuadParams& q,
+                                             const RadialView<T>& rv, T fu, T fv, int half,
+                                             double dw, int lane, unsigned long long& my_bad,
+                                             unsigned long long& my_nodes) {
+  constexpr int NC = RadialN<T>::n;   // Chebyshev points per piece
+  constexpr int NS = NC + 1;          // stride of a piece (offsets the banks)
+  constexpr int PPW = 32 / NC;        // pieces transformed per warp pass
+  const int max_pieces = rv.buf / NS;
+  const float adw = static_cast<float>(fabs(dw));
+  // farthest tap: |u offset| <= max(half - fu, fu + half - 1), likewise in v;
+  // the piece count is clamped to the storage the plan sized for its
+  // largest support (a rounding excess is extrapolated by the last piece)
+  const T mu = fmax(static_cast<T>(half) - fu, fu + static_cast<T>(half - 1));
+  const T mv = fmax(static_cast<T>(half) - fv, fv + static_cast<T>(half - 1));
+  const T pf = ceil(sqrt(mu * mu + mv * mv) * rv.inv_L);
+  int pieces = 1;
+  if (pf >= static_cast<T>(max_pieces)) pieces = max_pieces;
+  else if (pf > T(1)) pieces = static_cast<int>(pf);
+  const int npts = pieces * NC;
+  int built = 0;
+  // the kernel at the Chebyshev points, 32 at a time in increasing rho
+  for (int k0 = 0; k0 < npts; k0 += 32) {
+    const int k = k0 + lane;
+    const bool active = k < npts;
+    const int kk = active ? k : npts - 1;   // idle lanes repeat the last point
+    const int pc = kk / NC, j = kk - pc * NC;
+    const T rho = rv.L * (static_cast<T>(pc) + rv.x1[j]);
+    T rmax = rho;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+    const int npan = initial_panels(q, static_cast<float>(rmax), adw);
+    bool ok = true;
+    const C K = eval_chunk<T, C>(sh, q, rho, active, dw, npan, built, ok, lane, my_nodes);
+    if (active) {
+      ser[pc * NS + j] = K;
+      if (!ok) ++my_bad;
+    }
+  }
+  __syncwarp();
+  // c_m = (2 - [m == 0]) / NC sum_j f_j cos(pi m (j + 1/2) / NC), in place
+  for (int p0 = 0; p0 < pieces; p0 += PPW) {
+    const int pc = p0 + lane / NC, m = lane - (lane / NC) * NC;
+    const bool on = lane < PPW * NC && pc < pieces;
+    C c = cmake<C>(0.0, 0.0);
+    if (on) {
+      const C* f = ser + pc * NS;
+      const T* dc = rv.dct + m;
+#pragma unroll 4
+      for (int j = 0; j < NC; ++j) {
+        const T t = dc[j * NC];
+        const C v = f[j];
+        c.x = fma(v.x, t, c.x);
+        c.y = fma(v.y, t, c.y);
+      }
+      const T sc = (m == 0 ? T(1) : T(2)) / static_cast<T>(NC);
+      c.x *= sc;
+      c.y *= sc;
+    }
+    __syncwarp();
+    if (on) ser[pc * NS + m] = c;
+    __syncwarp();
+  }
+  for (int pc = lane; pc < pieces; pc += 32) {
+    const C* c = ser + pc * NS;
+    T cmax = 0;
+    for (int m = 0; m < NC; ++m) cmax = fmax(cmax, est_sqrt(c[m].x * c[m].x + c[m].y * c[m].y));
+    const T tail = est_sqrt(c[NC - 1].x * c[NC - 1].x + c[NC - 1].y * c[NC - 1].y) +
+                   est_sqrt(c[NC - 2].x * c[NC - 2].x + c[NC - 2].y * c[NC - 2].y);
+    if (!(tail <= fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * cmax))) ++my_bad;
+  }
+  return pieces;
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ C radial_eval(const C* ser, const RadialView<T>& rv, int last, T last_f,
+                                         T rho) {
+  constexpr int NC = RadialN<T>::n;
+  constexpr int NS = NC + 1;
+  int ip;
+  T fr;
+  table_index(rho * rv.inv_L, last, last_f, ip, fr);
+  const T x = fma(T(2), fr, T(-1));
+  const T x2 = x + x;
+  const C* c = ser + ip * NS;
+  // Clenshaw: b_m = 2 x b_{m+1} - b_{m+2} + c_m;  K = x b_1 - b_2 + c_0
+  T b1x = 0, b1y = 0, b2x = 0, b2y = 0;
+#pragma unroll
+  for (int m = NC - 1; m >= 1; --m) {
+    const C cm = c[m];
+    const T nx = fma(x2, b1x, cm.x - b2x);
+    const T ny = fma(x2, b1y, cm.y - b2y);
+    b2x = b1x;
+    b2y = b1y;
+    b1x = nx;
+    b1y = ny;
+  }
+  const C c0 = c[0];
+  C K;
+  K.x = fma(x, b1x, c0.x - b2x);
+  K.y = fma(x, b1y, c0.y - b2y);
+  return K;
+}
+
+// The radial mode's fused kernel: the series of each visibility, then every
+// tap evaluated from it.
 template <typename T, typename C, bool kGrid>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel(
     const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
@@ -865,16 +971,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
     C* __restrict__ vis_out, QuadParams q, RadialView<T> rv,
     const int32_t* __restrict__ stack_slot, unsigned long long* head,
     unsigned long long* stats, int batch) {
-  constexpr int NC = RadialN<T>::n;   // Chebyshev points per piece
-  constexpr int NS = NC + 1;          // stride of a piece (offsets the banks)
-  constexpr int PPW = 32 / NC;        // pieces transformed per warp pass
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   C* ser = reinterpret_cast<C*>(smem_raw + (blockDim.x >> 5) * kNodeBatch * sizeof(NodeVal<T>)) +
            warp * rv.buf;
-  const int max_pieces = rv.buf / NS;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int npad = q.npad;
   WarpQueue wq;
@@ -885,72 +987,12 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
     const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
     const int half = Jw / 2;
     const T fu = r.fu, fv = r.fv;
-    const float adw = static_cast<float>(fabs(r.dw));
     const uint32_t pm = perm[i];
     const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
                        : cmake<C>(0.0, 0.0);
-    // farthest tap: |u offset| <= max(half - fu, fu + half - 1), likewise in v;
-    // the piece count is clamped to the storage the plan sized for its
-    // largest support (a rounding excess is extrapolated by the last piece)
-    const T mu = fmax(static_cast<T>(half) - fu, fu + static_cast<T>(half - 1));
-    const T mv = fmax(static_cast<T>(half) - fv, fv + static_cast<T>(half - 1));
-    const T pf = ceil(sqrt(mu * mu + mv * mv) * rv.inv_L);
-    int pieces = 1;
-    if (pf >= static_cast<T>(max_pieces)) pieces = max_pieces;
-    else if (pf > T(1)) pieces = static_cast<int>(pf);
-    const int npts = pieces * NC;
-    int built = 0;
-    // 1. the kernel at the Chebyshev points, 32 at a time in increasing rho
-    for (int k0 = 0; k0 < npts; k0 += 32) {
-      const int k = k0 + lane;
-      const bool active = k < npts;
-      const int kk = active ? k : npts - 1;   // idle lanes repeat the last point
-      const int pc = kk / NC, j = kk - pc * NC;
-      const T rho = rv.L * (static_cast<T>(pc) + rv.x1[j]);
-      T rmax = rho;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-      const int npan = initial_panels(q, static_cast<float>(rmax), adw);
-      bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, built, ok, lane, my_nodes);
-      if (active) {
-        ser[pc * NS + j] = K;
-        if (!ok) ++my_bad;
-      }
-    }
-    __syncwarp();
-    // 2. c_m = (2 - [m == 0]) / NC sum_j f_j cos(pi m (j + 1/2) / NC), in place
-    for (int p0 = 0; p0 < pieces; p0 += PPW) {
-      const int pc = p0 + lane / NC, m = lane - (lane / NC) * NC;
-      const bool on = lane < PPW * NC && pc < pieces;
-      C c = cmake<C>(0.0, 0.0);
-      if (on) {
-        const C* f = ser + pc * NS;
-        const T* dc = rv.dct + m;
-#pragma unroll 4
-        for (int j = 0; j < NC; ++j) {
-          const T t = dc[j * NC];
-          const C v = f[j];
-          c.x = fma(v.x, t, c.x);
-          c.y = fma(v.y, t, c.y);
-        }
-        const T sc = (m == 0 ? T(1) : T(2)) / static_cast<T>(NC);
-        c.x *= sc;
-        c.y *= sc;
-      }
-      __syncwarp();
-      if (on) ser[pc * NS + m] = c;
-      __syncwarp();
-    }
-    for (int pc = lane; pc < pieces; pc += 32) {
-      const C* c = ser + pc * NS;
-      T cmax = 0;
-      for (int m = 0; m < NC; ++m) cmax = fmax(cmax, est_sqrt(c[m].x * c[m].x + c[m].y * c[m].y));
-      const T tail = est_sqrt(c[NC - 1].x * c[NC - 1].x + c[NC - 1].y * c[NC - 1].y) +
-                     est_sqrt(c[NC - 2].x * c[NC - 2].x + c[NC - 2].y * c[NC - 2].y);
-      if (!(tail <= fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * cmax))) ++my_bad;
-    }
-    // 3. every tap from its piece's series; taps t = b Jw + a in raster order,
+    const int pieces = radial_series<T, C>(ser, sh, q, rv, fu, fv, half, r.dw, lane, my_bad,
+                                           my_nodes);
+    // every tap from its piece's series; taps t = b Jw + a in raster order,
     // advanced by 32 per chunk without a division per tap
     C accv = cmake<C>(0.0, 0.0);
     const int ntap = Jw * Jw;
@@ -965,29 +1007,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
       const int t = t0 + lane;
       if (t < ntap) {
         const int ou = a - half + 1, ov = b - half + 1;
-        const T rho = sqrt(du_ * du_ + dv_ * dv_);
-        int ip;
-        T fr;
-        table_index(rho * rv.inv_L, last, last_f, ip, fr);
-        const T x = fma(T(2), fr, T(-1));
-        const T x2 = x + x;
-        const C* c = ser + ip * NS;
-        // Clenshaw: b_m = 2 x b_{m+1} - b_{m+2} + c_m;  K = x b_1 - b_2 + c_0
-        T b1x = 0, b1y = 0, b2x = 0, b2y = 0;
-#pragma unroll
-        for (int m = NC - 1; m >= 1; --m) {
-          const C cm = c[m];
-          const T nx = fma(x2, b1x, cm.x - b2x);
-          const T ny = fma(x2, b1y, cm.y - b2y);
-          b2x = b1x;
-          b2y = b1y;
-          b1x = nx;
-          b1y = ny;
-        }
-        const C c0 = c[0];
-        C K;
-        K.x = fma(x, b1x, c0.x - b2x);
-        K.y = fma(x, b1y, c0.y - b2y);
+        const C K = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
         ++my_taps;
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
@@ -1017,15 +1037,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
 
 // Degrid / grid with a separable DDE kernel D_i(s) = a_i(s_u) b_i(s_v)
 // (J_D = 2 h + 1 taps a side, caller's visibility order) convolved with the
-// w-kernel: the warp integrates the visibility's J_w x J_w w-kernel taps by
-// the per-tap quadrature into shared memory, then forms every tap of the
-// (J_w + J_D - 1)^2 box as C(q) = sum_s D(s) [GC](u - q - s), i.e. from the
-// stored taps K[q + s - q0].
-template <typename T, typename C, bool kGrid>
+// w-kernel: the warp fills the visibility's J_w x J_w w-kernel taps into
+// shared memory -- by the per-tap quadrature, or (kRadial) from the radial
+// mode's series -- then forms every tap of the (J_w + J_D - 1)^2 box as
+// C(q) = sum_s D(s) [GC](u - q - s), i.e. from the stored taps K[q + s - q0].
+template <typename T, typename C, bool kGrid, bool kRadial>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
     const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
     const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
-    C* __restrict__ vis_out, QuadParams q, const C* __restrict__ dde_a,
+    C* __restrict__ vis_out, QuadParams q, RadialView<T> rv, const C* __restrict__ dde_a,
     const C* __restrict__ dde_b, int jd, int box_max, const int32_t* __restrict__ stack_slot,
     unsigned long long* head, unsigned long long* stats, int batch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1033,8 +1053,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
   const int warp = threadIdx.x >> 5;
   NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
   C* box = reinterpret_cast<C*>(smem_raw + (blockDim.x >> 5) * kNodeBatch * sizeof(NodeVal<T>)) +
-           warp * (box_max * box_max + 2 * jd);
+           warp * (box_max * box_max + 2 * jd + (kRadial ? rv.buf : 0));
   C* dab = box + box_max * box_max;   // a_i then b_i
+  C* ser = dab + 2 * jd;              // kRadial: the visibility's series
   const int h = jd >> 1;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int npad = q.npad;
@@ -1054,8 +1075,20 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
     const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
                        : cmake<C>(0.0, 0.0);
     if (lane < 2 * jd) dab[lane] = lane < jd ? dde_a[src * jd + lane] : dde_b[src * jd + lane - jd];
-    // 1. the w-kernel on the J_w box, by the per-tap quadrature (ring order)
     const int ntap = Jw * Jw;
+    if (kRadial) {
+      // 1. the w-kernel on the J_w box from the visibility's series
+      const int pieces = radial_series<T, C>(ser, sh, q, rv, fu, fv, half, r.dw, lane, my_bad,
+                                             my_nodes);
+      const int last = pieces - 1;
+      const T last_f = static_cast<T>(last);
+      for (int t = lane; t < ntap; t += 32) {
+        const int kb = t / Jw, ka = t - kb * Jw;
+        const T du_ = fu - static_cast<T>(ka - half + 1), dv_ = fv - static_cast<T>(kb - half + 1);
+        box[t] = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
+      }
+    } else {
+    // 1. the w-kernel on the J_w box, by the per-tap quadrature (ring order)
     for (int t0 = 0; t0 < ntap; t0 += 32) {
       const int t = t0 + lane;
       const bool active = t < ntap;
@@ -1073,6 +1106,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
         box[kb * Jw + ka] = K;
         if (!ok) ++my_bad;
       }
+    }
     }
     __syncwarp();
     // 2. the combined taps, raster order over the J_w + 2 h box
@@ -1291,7 +1325,8 @@ struct DdeArgs {
 template <typename T, typename C>
 size_t dde_warp_smem(const Plan& p, int jd) {
   const size_t jmax = static_cast<size_t>(std::max(p.max_jw, 2));
-  return kNodeBatch * sizeof(NodeVal<T>) + (jmax * jmax + 2 * jd) * sizeof(C);
+  const size_t ser = p.d.kernel_mode == PHI_KERNEL_RADIAL ? p.radial_buf : 0;
+  return kNodeBatch * sizeof(NodeVal<T>) + (jmax * jmax + 2 * jd + ser) * sizeof(C);
 }
 
 template <typename T, typename C, bool kGrid>
@@ -1318,14 +1353,17 @@ int launch_dde(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, int g, co
   }
   if (warps < 1) return PHI_ERR_SUPPORT;
   const size_t smem = per_warp * warps;
+  const bool radial = p.d.kernel_mode == PHI_KERNEL_RADIAL;
+  auto kernel = radial ? vis_dde_kernel<T, C, kGrid, true> : vis_dde_kernel<T, C, kGrid, false>;
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vis_dde_kernel<T, C, kGrid>,
-                                                    32 * warps, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem) !=
+          cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   const int blocks = per_sm * p.num_sms;
-  vis_dde_kernel<T, C, kGrid><<<blocks, 32 * warps, smem, s>>>(
-      recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(),
+  const RadialView<T> rv = radial ? radial_view<T, C>(p) : RadialView<T>{};
+  kernel<<<blocks, 32 * warps, smem, s>>>(
+      recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(), rv,
       static_cast<const C*>(dde.a), static_cast<const C*>(dde.b), dde.jd, std::max(p.max_jw, 2),
       p.stack_slot_dev, p.counters + g, p.counters + p.K, queue_batch(nk, blocks * warps));
   PHI_CUDA_TRY(cudaGetLastError());
@@ -1487,6 +1525,16 @@ void timer_end(Plan& p, long idx, int stage, cudaStream_t s) {
   p.ev_pending.emplace_back(stage, static_cast<size_t>(idx));
 }
 
+template <typename T, typename C>
+cudaError_t set_dde_smem(int bytes) {
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(vis_dde_kernel<T, C, false, false>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(vis_dde_kernel<T, C, true, false>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(vis_dde_kernel<T, C, false, true>, a, bytes);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(vis_dde_kernel<T, C, true, true>, a, bytes);
+  return e;
+}
+
 int set_kernel_smem_limits() {
   const size_t f32 = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<float>);
   const size_t f64 = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<double>);
@@ -1519,14 +1567,8 @@ int set_kernel_smem_limits() {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   PHI_CUDA_TRY(cudaFuncSetAttribute(vis_radial_kernel<double, double2, true>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<float, float2, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<float, float2, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<double, double2, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
-  PHI_CUDA_TRY(cudaFuncSetAttribute(vis_dde_kernel<double, double2, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  PHI_CUDA_TRY((set_dde_smem<float, float2>(optin)));
+  PHI_CUDA_TRY((set_dde_smem<double, double2>(optin)));
   return PHI_OK;
 }
 

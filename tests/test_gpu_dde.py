@@ -92,7 +92,8 @@ def test_dde_delta_and_shifted_delta(case):
 
 
 def test_dde_in_a_radial_mode_plan(case):
-    """The DDE path integrates the w-kernel box per tap whatever the mode."""
+    """In a radial-mode plan the w-kernel box comes from the visibility's
+    Chebyshev series: the same operator within the quadrature tolerance."""
     plan = gpu_plan(case["uvw"], case["geo"], 3, False, "f32", kernel_mode="radial")
     y = plan.degrid_dde(to_t(case["x"], torch.float32), case["a"], case["b"]).cpu().numpy()
     assert O.rel_l2(y, case["y_ref"]) < TOL32
