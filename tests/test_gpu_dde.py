@@ -28,17 +28,18 @@ def case():
     uvw = W.uvw_disk(600, 60.0, 40.0, 71)
     h = geo.Npad / 2 * geo.du
     uvw[:2, 0] = [h - 0.4 * geo.du, -h + 0.3 * geo.du]   # combined boxes across the edge
-    op = O.make_plan(uvw, geo, 3, False)
+    wts = np.linspace(0.5, 1.5, len(uvw))
+    op = O.make_plan(uvw, geo, 3, False, weights=wts)
     a, b = W.dde_kernels(len(uvw), 5, 72)
     x = W.point_sources(128, 20, 73)
     yr = W.random_vis(len(uvw), 74)
-    return dict(geo=geo, uvw=uvw, op=op, a=a, b=b, x=x, yr=yr,
+    return dict(geo=geo, uvw=uvw, w=wts, op=op, a=a, b=b, x=x, yr=yr,
                 y_ref=O.degrid_dde(op, x, a, b), x_ref=O.grid_dde(op, yr, a, b))
 
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_dde_matches_oracle(case, precision):
-    plan = gpu_plan(case["uvw"], case["geo"], 3, False, precision)
+    plan = gpu_plan(case["uvw"], case["geo"], 3, False, precision, case["w"])
     rd, cd, tol = dtypes(precision)
     y = plan.degrid_dde(to_t(case["x"], rd), case["a"], case["b"]).cpu().numpy()
     assert O.rel_l2(y, case["y_ref"]) < tol
@@ -50,7 +51,7 @@ def test_dde_matches_oracle(case, precision):
 
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_dde_adjoint_dot_product(case, precision):
-    plan = gpu_plan(case["uvw"], case["geo"], 3, False, precision)
+    plan = gpu_plan(case["uvw"], case["geo"], 3, False, precision, case["w"])
     rd, cd, _ = dtypes(precision)
     x = to_t(W.random_image(128, 75), rd)
     y = to_t(W.random_vis(len(case["uvw"]), 76), cd)
@@ -94,7 +95,7 @@ def test_dde_delta_and_shifted_delta(case):
 def test_dde_in_a_radial_mode_plan(case):
     """In a radial-mode plan the w-kernel box comes from the visibility's
     Chebyshev series: the same operator within the quadrature tolerance."""
-    plan = gpu_plan(case["uvw"], case["geo"], 3, False, "f32", kernel_mode="radial")
+    plan = gpu_plan(case["uvw"], case["geo"], 3, False, "f32", case["w"], kernel_mode="radial")
     y = plan.degrid_dde(to_t(case["x"], torch.float32), case["a"], case["b"]).cpu().numpy()
     assert O.rel_l2(y, case["y_ref"]) < TOL32
 
