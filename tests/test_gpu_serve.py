@@ -81,3 +81,28 @@ def test_budget_rejects_oversized_request():
     with S.Server(hbm_budget_bytes=S.estimate_bytes(req) // 2, slots=2) as srv:
         res = srv.run_stream([req], realtime=False)[0]
     assert res.status == "error" and "budget" in res.error
+
+
+@pytest.mark.parametrize("image_n,k,m,raise_stacks", [(256, 64, 20000, False),
+                                                      (1024, 8, 50000, False),
+                                                      (512, 4, 20000, True)])
+def test_admission_estimate_bounds_the_plan(image_n, k, m, raise_stacks):
+    """The admission estimate is at least the plan's own device bytes (its
+    allocations and cuFFT workspace, as the library reports them) plus the
+    request's inputs and outputs: small images with many stacks keep a whole
+    group of grids resident, and a raised request may double its stacks."""
+    fov = math.radians(20.0)
+    radius = 0.3 * image_n / (2 * fov) / 2
+    wmax = 800.0 if raise_stacks else 60.0
+    uvw = W.uvw_disk(m, radius, wmax, 5)
+    desc = dict(image_n=image_n, fov_rad=fov, n_stacks=k, conj_fold=1, max_support=32)
+    req = S.Request(0, uvw, desc, image=W.point_sources(image_n, 4, 5), ops=("degrid", "grid"),
+                    raise_stacks=raise_stacks)
+    est = S.estimate_bytes(req)
+    with S.Server(hbm_budget_bytes=1 << 38, slots=1) as srv:
+        res = srv.run_stream([req], realtime=False)[0]
+    assert res.status == "ok", res.error
+    if raise_stacks:
+        assert res.n_stacks > k
+    io = m * 2 * 8 + image_n * image_n * 2 * 4
+    assert res.device_bytes + io <= est, (res.device_bytes, est)
