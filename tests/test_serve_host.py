@@ -1,0 +1,42 @@
+"""Host logic of the serving engine that needs no GPU: the admission estimate
+charges the padded grids of a plan's whole stack group (up to max_grid_mib),
+the most stacks a raised request can reach, and only inputs and outputs for
+a resident plan."""
+import math
+
+import numpy as np
+
+from paper_1903_06555_gb300 import serve as S
+
+
+def req(n, k, m=10000, raise_stacks=False, **desc):
+    d = dict(image_n=n, fov_rad=math.radians(20.0), n_stacks=k)
+    d.update(desc)
+    return S.Request(0, np.zeros((m, 3)), d, raise_stacks=raise_stacks)
+
+
+def test_grids_of_the_whole_group_are_charged():
+    grid = 8 * 1024 * 1024                      # 512^2 image, 1024^2 complex64 grid
+    e1, e8, e64 = (S.estimate_bytes(req(512, k)) for k in (1, 8, 64))
+    assert e8 - e1 == 2 * 7 * grid              # group grids + batched workspace
+    assert e64 - e8 == 2 * 56 * grid
+
+
+def test_group_is_capped_by_max_grid_mib():
+    grid = 8 * 16384 * 16384                    # 8192^2 image: 2 GiB per grid
+    e2, e64 = (S.estimate_bytes(req(8192, k)) for k in (2, 64))
+    assert e64 == e2                            # 4 GiB default: 2 grids per group
+    small_cap = S.estimate_bytes(req(8192, 64, max_grid_mib=2048))
+    assert e2 - small_cap == 2 * grid
+
+
+def test_raised_requests_are_charged_for_126_stacks():
+    assert S.estimate_bytes(req(512, 4, raise_stacks=True)) == S.estimate_bytes(req(512, 126))
+
+
+def test_resident_plan_charges_inputs_and_outputs_only():
+    r = req(512, 8, m=20000)
+    io = 20000 * 2 * 8 + 512 * 512 * 2 * 4 + (16 << 20)
+    assert S.estimate_bytes(r, planned=True) == io
+    r64 = req(512, 8, m=20000, precision="f64")
+    assert S.estimate_bytes(r64, planned=True) == 20000 * 2 * 16 + 512 * 512 * 2 * 8 + (16 << 20)
