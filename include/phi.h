@@ -298,7 +298,9 @@ int phi_grid_dde(phi_plan_t plan, const void* vis_dev, const void* dde_a_dev,
  *   rho_dev: n float64 radii in grid pixels (>= 0); dw_dev: n float64 w offsets.
  *   k_dev:   n complex outputs (float32 or float64 pairs per precision).
  *   n_unconverged: host pointer or NULL; when non-NULL the call synchronises
- *   `stream` and stores the number of points that missed the tolerance.
+ *   `stream` and stores the number of points that missed the tolerance (a
+ *   synchronisation is not allowed while `stream` is being captured into a
+ *   graph: such a call returns PHI_ERR_ARG and launches nothing).
  */
 int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, int64_t n,
                 void* k_dev, int64_t* n_unconverged, void* stream);
@@ -320,8 +322,9 @@ int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, in
  *
  *   params:  geometry and quadrature settings (below); max_panels must be in
  *            1..PHI_WKERNEL_NOALLOC_MAX_PANELS, otherwise PHI_ERR_ARG and
- *            nothing runs.  Points that would need more panels are evaluated
- *            with max_panels and counted as unconverged.
+ *            nothing runs.  Refinement doubles the panels up to max_panels;
+ *            points still above the tolerance there (or after max_refine
+ *            doublings) are counted as unconverged.
  *   rho_dev, dw_dev, n, k_dev, n_unconverged, stream: as for phi_wkernel.
  *
  * The first call on a device looks up the array's device address (once per

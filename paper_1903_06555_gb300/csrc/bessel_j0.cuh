@@ -6,7 +6,8 @@
 // J0 = M0 cos theta0 (A&S 9.2.17) with sqrt(u) M0 and the phase correction
 // as degree-4 polynomials in 1/u^2 (the parities of their Hankel expansions,
 // A&S 9.2.28-9.2.31), coefficients fitted by j0_fit.py in this directory
-// (|error| < 5.2e-8).
+// (|error| < 5.2e-8); for u >= 2 the same form with both polynomials of
+// degree 2 (|error| < 4.7e-8, two multiply-adds fewer per polynomial).
 // The phase theta0 = pi (u + D/u) - pi/4 is formed in FP32 and handed to the
 // hardware cosine, which reduces it by whole turns itself.  The argument's own
 // FP32 rounding (relative 6e-8, i.e. 6e-6 rad at 100 rad, the largest phase a
@@ -95,5 +96,79 @@ PHI_HD inline float j0_large(float u) {
 PHI_HD inline float j0_halfcycles(float u) {
   return u <= kJ0Split ? j0_small(u) : j0_large(u);
 }
+
+// Lower end of the degree-2 form: x = pi u = 2 pi.
+constexpr float kJ0Far = 2.0f;
+
+// J0(pi u) for u >= kJ0Far: j0_large's form with F and D of degree 2 (the
+// fit of j0_fit.py on [2, 1e5]; J0 error <= 3.9e-8 from F, 8.5e-9 from D).
+PHI_HD inline float j0_far(float u) {
+  const float r = j0_rsqrt(u);
+  const float s = r * r;
+  const float q = s * s;
+  float f = 3.987198814e-04f;
+  f = j0_fma(f, q, -2.842591913e-03f);
+  f = j0_fma(f, q, 4.501579747e-01f);
+  float d = -1.628429337e-04f;
+  d = j0_fma(d, q, 6.617906817e-04f);
+  d = j0_fma(d, q, -1.266492407e-02f);
+  const float phi = j0_fma(d, s, u);
+  return (r * f) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
+}
+
+#if defined(__CUDACC__)
+// Two arguments at once in Blackwell's paired FP32 arithmetic (f32x2 FMA
+// and multiply, one instruction for both halves): the same operations, in
+// the same order and rounding, as j0_small, j0_large and j0_far on each
+// half.
+__device__ __forceinline__ float2 j0_pair(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ float2 j0_small2(float2 u) {
+  const float2 z = __fmul2_rn(__fmul2_rn(u, u), j0_pair(1.096622711232151f, 1.096622711232151f));
+  float2 p = j0_pair(0.0002100f, 0.0002100f);
+  p = __ffma2_rn(p, z, j0_pair(-0.0039444f, -0.0039444f));
+  p = __ffma2_rn(p, z, j0_pair(0.0444479f, 0.0444479f));
+  p = __ffma2_rn(p, z, j0_pair(-0.3163866f, -0.3163866f));
+  p = __ffma2_rn(p, z, j0_pair(1.2656208f, 1.2656208f));
+  p = __ffma2_rn(p, z, j0_pair(-2.2499997f, -2.2499997f));
+  return __ffma2_rn(p, z, j0_pair(1.0f, 1.0f));
+}
+
+__device__ __forceinline__ float2 j0_large2(float2 u) {
+  const float2 r = j0_pair(j0_rsqrt(u.x), j0_rsqrt(u.y));
+  const float2 s = __fmul2_rn(r, r);
+  const float2 q = __fmul2_rn(s, s);
+  float2 f = j0_pair(2.949163237e-05f, 2.949163237e-05f);
+  f = __ffma2_rn(f, q, j0_pair(-1.386496738e-04f, -1.386496738e-04f));
+  f = __ffma2_rn(f, q, j0_pair(4.440745370e-04f, 4.440745370e-04f));
+  f = __ffma2_rn(f, q, j0_pair(-2.846068740e-03f, -2.846068740e-03f));
+  f = __ffma2_rn(f, q, j0_pair(4.501580035e-01f, 4.501580035e-01f));
+  float2 d = j0_pair(-1.531106734e-05f, -1.531106734e-05f);
+  d = __ffma2_rn(d, q, j0_pair(6.988119170e-05f, 6.988119170e-05f));
+  d = __ffma2_rn(d, q, j0_pair(-1.853455306e-04f, -1.853455306e-04f));
+  d = __ffma2_rn(d, q, j0_pair(6.629692300e-04f, 6.629692300e-04f));
+  d = __ffma2_rn(d, q, j0_pair(-1.266485270e-02f, -1.266485270e-02f));
+  const float2 phi = __ffma2_rn(d, s, u);
+  const float2 th = __ffma2_rn(phi, j0_pair(3.14159265358979f, 3.14159265358979f),
+                               j0_pair(-0.785398163397448f, -0.785398163397448f));
+  return __fmul2_rn(__fmul2_rn(r, f), j0_pair(j0_cos(th.x), j0_cos(th.y)));
+}
+
+__device__ __forceinline__ float2 j0_far2(float2 u) {
+  const float2 r = j0_pair(j0_rsqrt(u.x), j0_rsqrt(u.y));
+  const float2 s = __fmul2_rn(r, r);
+  const float2 q = __fmul2_rn(s, s);
+  float2 f = j0_pair(3.987198814e-04f, 3.987198814e-04f);
+  f = __ffma2_rn(f, q, j0_pair(-2.842591913e-03f, -2.842591913e-03f));
+  f = __ffma2_rn(f, q, j0_pair(4.501579747e-01f, 4.501579747e-01f));
+  float2 d = j0_pair(-1.628429337e-04f, -1.628429337e-04f);
+  d = __ffma2_rn(d, q, j0_pair(6.617906817e-04f, 6.617906817e-04f));
+  d = __ffma2_rn(d, q, j0_pair(-1.266492407e-02f, -1.266492407e-02f));
+  const float2 phi = __ffma2_rn(d, s, u);
+  const float2 th = __ffma2_rn(phi, j0_pair(3.14159265358979f, 3.14159265358979f),
+                               j0_pair(-0.785398163397448f, -0.785398163397448f));
+  return __fmul2_rn(__fmul2_rn(r, f), j0_pair(j0_cos(th.x), j0_cos(th.y)));
+}
+#endif
 
 }  // namespace phi

@@ -8,10 +8,12 @@ polynomials in q = 1/u^2:
 
     J0(pi u) = u^{-1/2} F(q) cos(pi (u + D(q) / u) - pi/4),
 
-F and D of degree 4 in q.  The coefficients minimise the largest absolute
-error of J0 this form gives (the L-infinity fit, solved as a linear program on
-a dense grid of u in [3/pi, 1e5]), separately for the modulus and the phase
-part, against scipy's j0 and y0.  Run it to print the constants.
+F and D of degree 4 in q for u >= 3/pi, and of degree 2 for u >= 2 (x >= 2 pi),
+where the Hankel series converge fast enough that the lower degree keeps the
+same accuracy.  The coefficients minimise the largest absolute error of J0
+this form gives (the L-infinity fit, solved as a linear program on a dense
+grid of u in [u_min, 1e5]), separately for the modulus and the phase part,
+against scipy's j0 and y0.  Run it to print the constants of both fits.
 """
 import numpy as np
 import scipy.optimize as so
@@ -19,6 +21,8 @@ import scipy.special as sp
 
 U_MIN = 3.0 / np.pi
 DEGREE = 4
+U_MIN_FAR = 2.0
+DEGREE_FAR = 2
 
 
 def modulus_and_phase(u):
@@ -48,34 +52,36 @@ def linf_fit(a, y, w, scale=1e8):
     return res.x[:k]
 
 
-def fit(n=20000):
-    u = np.geomspace(U_MIN, 1e5, n)
+def fit(n=20000, u_min=U_MIN, degree=DEGREE):
+    u = np.geomspace(u_min, 1e5, n)
     q = 1.0 / u ** 2
-    qmax = 1.0 / U_MIN ** 2
+    qmax = 1.0 / u_min ** 2
     f, d = modulus_and_phase(u)
     r = 1.0 / np.sqrt(u)
     # columns in the normalised variable q / qmax, so all lie in [0, 1]
-    a = np.vander(q / qmax, DEGREE + 1, increasing=True)
-    back = qmax ** -np.arange(DEGREE + 1)
+    a = np.vander(q / qmax, degree + 1, increasing=True)
+    back = qmax ** -np.arange(degree + 1)
     # J0 error: r * (F error) from the modulus, (F r) (pi / u) * (D error) from the phase
     cf = linf_fit(a, f, r) * back
     cd = linf_fit(a, d, f * r * np.pi / u) * back
     return cf, cd
 
 
-def max_errors(cf, cd, n=300001):
+def max_errors(cf, cd, n=300001, u_min=U_MIN):
     """Largest J0 error of each part on a grid 15x denser than the fit's."""
-    u = np.geomspace(U_MIN, 1e5, n)
+    u = np.geomspace(u_min, 1e5, n)
     q = 1.0 / u ** 2
     f, d = modulus_and_phase(u)
     r = 1.0 / np.sqrt(u)
-    a = np.vander(q, DEGREE + 1, increasing=True)
+    a = np.vander(q, len(cf), increasing=True)
     return (np.max(r * np.abs(a @ cf - f)), np.max(f * r * np.pi / u * np.abs(a @ cd - d)))
 
 
 if __name__ == "__main__":
-    cf, cd = fit()
-    ef, ed = max_errors(cf, cd)
-    print(f"// max |J0 error| from the modulus {ef:.2e}, from the phase {ed:.2e}")
-    print("F:", ", ".join(f"{c:.9e}f" for c in cf))
-    print("D:", ", ".join(f"{c:.9e}f" for c in cd))
+    for u_min, degree in ((U_MIN, DEGREE), (U_MIN_FAR, DEGREE_FAR)):
+        cf, cd = fit(u_min=u_min, degree=degree)
+        ef, ed = max_errors(cf, cd, u_min=u_min)
+        print(f"// u >= {u_min:.6f}, degree {degree}: max |J0 error| from the modulus "
+              f"{ef:.2e}, from the phase {ed:.2e}")
+        print("F:", ", ".join(f"{c:.9e}f" for c in cf))
+        print("D:", ", ".join(f"{c:.9e}f" for c in cd))

@@ -213,6 +213,15 @@ struct Plan {
     }                                            \
   } while (0)
 
+// Calls that read a result back synchronise their stream, which is not
+// allowed while the stream is being captured into a graph: refuse them.
+#define PHI_TRY_NOT_CAPTURING(stream)                                   \
+  do {                                                                  \
+    cudaStreamCaptureStatus cs_ = cudaStreamCaptureStatusNone;          \
+    PHI_CUDA_TRY(cudaStreamIsCapturing((stream), &cs_));                \
+    if (cs_ != cudaStreamCaptureStatusNone) return PHI_ERR_ARG;         \
+  } while (0)
+
 // Kernel-side view of the pre-sampled w-planes.
 template <typename T>
 struct TableView {

@@ -68,6 +68,9 @@ __host__ __device__ constexpr double gk_wk(int j) { return gk_kronrod_weight(gk_
 __host__ __device__ constexpr double gk_wd(int j) {  // Kronrod minus Gauss weight
   return gk_kronrod_weight(gk_fold(j)) - gk_gauss_weight(gk_fold(j));
 }
+__host__ __device__ constexpr double gk_gw(int j) {  // Gauss weight (0: Kronrod-only node)
+  return gk_gauss_weight(gk_fold(j));
+}
 
 // Nodes in the precision of the integrand, read uniformly by the whole warp.
 __constant__ float c_gk_node_f[15] = {
@@ -181,7 +184,9 @@ __global__ void node_table_kernel(double R, double du, double a, double beta, do
   omn[j] = s / (1.0 + sqrt(1.0 - s));
   double h = 2.0 * kPi * hw * taper_g(r, a, beta, cyl_bessel_i0(beta)) * r;
   hk[j] = static_cast<T>(gk_wk(k) * h);
-  hd[j] = static_cast<T>(gk_wd(k) * h);
+  // FP32 quadrature forms its estimate from panel sums with the Gauss weight
+  // (zero at Kronrod-only nodes), FP64 from the Kronrod-minus-Gauss weight
+  hd[j] = static_cast<T>((sizeof(T) == 4 ? gk_gw(k) : gk_wd(k)) * h);
 }
 
 template <typename T>
@@ -306,7 +311,8 @@ __global__ void finish_kernel(const C* __restrict__ grids, const double* __restr
 // ---------------------------------------------------------------------------
 
 // Build the weighted integrand values for panels [p0, p0 + np) of the
-// npan-panel partition: h(r_j) e^{2 pi i dw (1 - n(r_j))}, phase argument in FP64.
+// npan-panel partition: h(r_j) e^{2 pi i dw (1 - n(r_j))}, phase argument in
+// FP64, one NodeVal per node (FP64 path: Kronrod and difference weights).
 template <typename T>
 __device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q, int npan, int p0,
                                             int np, double dw, int lane) {
@@ -329,12 +335,59 @@ __device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q,
   }
 }
 
+// FP32 panels are evaluated two nodes at a time in Blackwell's paired FP32
+// arithmetic.  A panel's 15 nodes then sit in kSlots float4 slots:
+//   slot m (m = 0..6)      the node pair (m, 14 - m), i.e. x = -|x_m| (lo) and
+//                          +|x_m| (hi): {w_K h cos lo, hi, w_K h sin lo, hi};
+//   slot 7 + i (i = 0..2)  the Gauss nodes among them (m = 2 i + 1): the same
+//                          with the Gauss weight w_G;
+//   slot 10                the centre node {w_K h cos, w_K h sin, w_G h cos,
+//                          w_G h sin}.
+// The FP32 node tables hold w_K h and w_G h (zero at Kronrod-only nodes).
+constexpr int kSlots = 11;
+static_assert(kSlots * 16 * kPanelBatch <= kNodeBatch * static_cast<int>(sizeof(NodeVal<float>)),
+              "packed panels must fit the per-warp node buffer");
+
+__device__ __forceinline__ void build_nodes(NodeVal<float>* sh, const QuadParams& q, int npan,
+                                            int p0, int np, double dw, int lane) {
+  const int64_t off = panel_table_offset(npan) + 15 * (int64_t)p0;
+  const double* omn = q.node_omn + off;
+  const float* hk = static_cast<const float*>(q.node_hk) + off;
+  const float* hg = static_cast<const float*>(q.node_hd) + off;
+  float* shf = reinterpret_cast<float*>(sh);
+  for (int j = lane; j < 15 * np; j += 32) {
+    double t = dw * omn[j];
+    t -= rint(t);
+    float sn, cs;
+    sincospif(static_cast<float>(2.0 * t), &sn, &cs);
+    const float k = hk[j], g = hg[j];
+    const int p = j / 15, n = j - 15 * p;
+    float* base = shf + 4 * kSlots * p;
+    if (n == 7) {
+      base[40] = k * cs;
+      base[41] = k * sn;
+      base[42] = g * cs;
+      base[43] = g * sn;
+    } else {
+      const int hi = n > 7 ? 1 : 0;
+      const int m = hi ? 14 - n : n;
+      base[4 * m + hi] = k * cs;
+      base[4 * m + 2 + hi] = k * sn;
+      if (m & 1) {
+        base[4 * (7 + (m >> 1)) + hi] = g * cs;
+        base[4 * (7 + (m >> 1)) + 2 + hi] = g * sn;
+      }
+    }
+  }
+}
+
 // Accumulate panels [0, np) held in sh (global panel index p0 + p) for one
 // tap: Bh = 2 rho h (half-cycles of J0 per unit of the node coordinate).
 // Every node of panel p lies in [a - Bh, a + Bh], a = Bh (2 (p0 + p) + 1);
 // when that whole range is past J0's small-argument formula for every active
 // lane of the warp, the panel runs an unrolled body with the asymptotic
 // formula only (the same values j0_hc gives there), with no per-node branch.
+// FP64 path: the error estimate sums |sum_j (w_K - w_G)_j f_j| per panel.
 template <typename T, bool kLarge>
 __device__ __forceinline__ void panel_nodes(const NodeVal<T>* hp, T Bh, T a, T& kr, T& ki, T& dr,
                                             T& di) {
@@ -365,44 +418,119 @@ __device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np
   }
 }
 
+// One FP32 panel: the seven node pairs in f32x2 arithmetic, the centre node
+// alone.  kMode 2: every node lies past kJ0Far (degree-2 asymptotic form);
+// 1: past J0's split (degree-4 form); 0: the panel straddles the split for
+// some lane, and both the small-argument and the asymptotic form are
+// evaluated and selected per node (no per-node branch).  Returns the panel's
+// Kronrod sum (kr, ki) and Gauss sum (gr, gi).
+template <int kMode>
+__device__ __forceinline__ void panel_pairs(const float4* hp, float Bh, float a, float& kr,
+                                            float& ki, float& gr, float& gi) {
+  float2 KR = make_float2(0.f, 0.f), KI = KR, GR = KR, GI = KR;
+#pragma unroll
+  for (int m = 0; m < 7; ++m) {
+    const float x = static_cast<float>(gk_abs_node(m));
+    const float2 u = make_float2(fmaf(-x, Bh, a), fmaf(x, Bh, a));
+    float2 J;
+    if (kMode == 2) {
+      J = j0_far2(u);
+    } else if (kMode == 1) {
+      J = j0_large2(u);
+    } else {
+      const float2 Js = j0_small2(u), Jl = j0_large2(u);
+      J = make_float2(u.x > kJ0Split ? Jl.x : Js.x, u.y > kJ0Split ? Jl.y : Js.y);
+    }
+    const float4 v = hp[m];
+    KR = __ffma2_rn(J, make_float2(v.x, v.y), KR);
+    KI = __ffma2_rn(J, make_float2(v.z, v.w), KI);
+    if (m & 1) {
+      const float4 g = hp[7 + (m >> 1)];
+      GR = __ffma2_rn(J, make_float2(g.x, g.y), GR);
+      GI = __ffma2_rn(J, make_float2(g.z, g.w), GI);
+    }
+  }
+  const float Jc = kMode == 2 ? j0_far(a) : kMode == 1 ? j0_large(a) : j0_halfcycles(a);
+  const float4 c = hp[10];
+  kr = fmaf(Jc, c.x, KR.x + KR.y);
+  ki = fmaf(Jc, c.y, KI.x + KI.y);
+  gr = fmaf(Jc, c.z, GR.x + GR.y);
+  gi = fmaf(Jc, c.w, GI.x + GI.y);
+}
+
+// FP32: per panel, the Kronrod sum K_p and the Gauss sum G_p; the estimate
+// adds |K_p - G_p|, formed from the panel's own sums (of the panel's size,
+// not the whole integral's).  The panel's formula is chosen by warp votes on
+// its lowest node argument a - Bh.
+__device__ __forceinline__ void eval_panels(const NodeVal<float>* sh, int p0, int np, float Bh,
+                                            bool active, float& kr, float& ki, float& err) {
+  const float4* hp = reinterpret_cast<const float4*>(sh);
+  float f = static_cast<float>(2 * p0 + 1);   // 2 (p0 + p) + 1, exact
+  for (int p = 0; p < np; ++p, f += 2.f, hp += kSlots) {
+    const float a = Bh * f;
+    const float lo = a - Bh;
+    float pkr, pki, pgr, pgi;
+    if (__all_sync(0xffffffffu, !active || lo >= kJ0Far))
+      panel_pairs<2>(hp, Bh, a, pkr, pki, pgr, pgi);
+    else if (__all_sync(0xffffffffu, !active || lo > kJ0Split))
+      panel_pairs<1>(hp, Bh, a, pkr, pki, pgr, pgi);
+    else
+      panel_pairs<0>(hp, Bh, a, pkr, pki, pgr, pgi);
+    kr += pkr;
+    ki += pki;
+    const float dr = pkr - pgr, di = pki - pgi;
+    err += est_sqrt(dr * dr + di * di);
+  }
+}
+
+// Half-cycles of J0 per unit node coordinate for a tap at rho on npan
+// panels: 2 rho R / (2 npan).
+__device__ __forceinline__ float panel_bh(const QuadParams& q, float rho, int npan) {
+  return (q.Rf / static_cast<float>(npan)) * rho;
+}
+__device__ __forceinline__ double panel_bh(const QuadParams& q, double rho, int npan) {
+  return (q.R / npan) * rho;
+}
+
 // Evaluate [GC](rho, dw) for one tap per lane (inactive lanes compute a
 // harmless dummy) on npan panels, doubling the panels for the whole chunk
-// while any active tap misses the tolerance.  `built` (the panel count whose
-// nodes are resident in sh, or 0) is warp-uniform and updated.
+// while any active tap misses the tolerance, up to max_panels (the node
+// tables' largest partition) and max_refine doublings.  `built` (the panel
+// count whose nodes are resident in sh, or 0) is warp-uniform and updated.
 template <typename T, typename C>
 __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active, double dw,
-                        int npan, int& built, bool& ok, int lane, unsigned long long& nodes) {
+                        int npan, int max_panels, int& built, bool& ok, int lane,
+                        unsigned long long& nodes) {
+  npan = min(npan, max_panels);
   int refine = 0;
   while (true) {
     nodes += active ? 15ull * npan : 0ull;
-    const T Bh = static_cast<T>(q.R / npan) * rho;   // 2 rho (R / (2 npan)), R/npan in FP64
+    const T Bh = panel_bh(q, rho, npan);
     T kr = 0, ki = 0, err = 0;
     if (npan <= kPanelBatch) {
       if (built != npan) {
         __syncwarp();
-        build_nodes<T>(sh, q, npan, 0, npan, dw, lane);
+        build_nodes(sh, q, npan, 0, npan, dw, lane);
         __syncwarp();
         built = npan;
       }
-      eval_panels<T>(sh, 0, npan, Bh, active, kr, ki, err);
+      eval_panels(sh, 0, npan, Bh, active, kr, ki, err);
     } else {
       for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
         const int nb = min(kPanelBatch, npan - p0);
         __syncwarp();
-        build_nodes<T>(sh, q, npan, p0, nb, dw, lane);
+        build_nodes(sh, q, npan, p0, nb, dw, lane);
         __syncwarp();
-        eval_panels<T>(sh, p0, nb, Bh, active, kr, ki, err);
+        eval_panels(sh, p0, nb, Bh, active, kr, ki, err);
       }
       built = 0;
     }
-    // err and |K| are both formed without cancellation (err from the
-    // Kronrod-minus-Gauss weights), so the test runs in T.
     const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * est_sqrt(kr * kr + ki * ki));
     ok = (!active) || err <= lim;
     const bool any_bad = __any_sync(0xffffffffu, !ok);
-    if (!any_bad || refine >= q.max_refine || 2 * npan > kMaxPanels) return cmake<C>(kr, ki);
+    if (!any_bad || refine >= q.max_refine || npan >= max_panels) return cmake<C>(kr, ki);
     ++refine;
-    npan *= 2;
+    npan = min(2 * npan, max_panels);
   }
 }
 
@@ -548,7 +676,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
       for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
       const int npan = initial_panels(q, static_cast<float>(rmax), adw);
       bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, built, ok, lane, my_nodes);
+      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, kMaxPanels, built, ok, lane, my_nodes);
       if (active) {
         ++my_taps;
         if (!ok) ++my_bad;
@@ -592,7 +720,7 @@ __global__ void __launch_bounds__(256) table_sample_kernel(C* __restrict__ raw, 
       const int64_t ilast = min(i0 + 31, nr - 1);
       const int npan = initial_panels(q, static_cast<float>(ilast * hr), static_cast<float>(w));
       bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, w, npan, built, ok, lane, nodes);
+      const C K = eval_chunk<T, C>(sh, q, rho, active, w, npan, kMaxPanels, built, ok, lane, nodes);
       if (active) raw[j * nr + i] = K;
     }
   }
@@ -839,7 +967,7 @@ __global__ void __launch_bounds__(256) wkernel_kernel(const double* __restrict__
     const C K = eval_chunk<T, C>(sh, q, rho, lane == 0, dw,
                                  initial_panels(q, static_cast<float>(rho),
                                                 static_cast<float>(fabs(dw))),
-                                 built, ok, lane, nodes);
+                                 kMaxPanels, built, ok, lane, nodes);
     if (lane == 0) {
       out[i] = K;
       if (!ok) atomicAdd(bad, 1ULL);
@@ -891,7 +1019,7 @@ __device__ __forceinline__ int radial_series(C* ser, NodeVal<T>* sh, const QuadP
     for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
     const int npan = initial_panels(q, static_cast<float>(rmax), adw);
     bool ok = true;
-    const C K = eval_chunk<T, C>(sh, q, rho, active, dw, npan, built, ok, lane, my_nodes);
+    const C K = eval_chunk<T, C>(sh, q, rho, active, dw, npan, kMaxPanels, built, ok, lane, my_nodes);
     if (active) {
       ser[pc * NS + j] = K;
       if (!ok) ++my_bad;
@@ -1101,7 +1229,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
       for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
       const int npan = initial_panels(q, static_cast<float>(rmax), adw);
       bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, built, ok, lane, my_nodes);
+      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, kMaxPanels, built, ok, lane, my_nodes);
       if (active) {
         box[kb * Jw + ka] = K;
         if (!ok) ++my_bad;
@@ -1644,6 +1772,7 @@ extern "C" int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double*
   if (!plan || n < 0 || (n > 0 && (!rho_dev || !dw_dev || !k_dev))) return PHI_ERR_ARG;
   phi::Plan& p = *plan;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_unconverged) PHI_TRY_NOT_CAPTURING(s);
   if (p.d.precision == PHI_F64)
     return phi::run_wkernel<double, double2>(p, rho_dev, dw_dev, n, static_cast<double2*>(k_dev),
                                              n_unconverged, s);
@@ -1725,42 +1854,6 @@ int noalloc_scratch(unsigned char** out) {
   return PHI_OK;
 }
 
-// eval_chunk with the panel count capped at the scratch tables' maximum.
-template <typename T, typename C>
-__device__ C eval_chunk_capped(NodeVal<T>* sh, const QuadParams& q, T rho, bool active, double dw,
-                               int npan, int max_panels, int& built, bool& ok, int lane) {
-  npan = min(npan, max_panels);
-  int refine = 0;
-  while (true) {
-    const T Bh = static_cast<T>(q.R / npan) * rho;
-    T kr = 0, ki = 0, err = 0;
-    if (npan <= kPanelBatch) {
-      if (built != npan) {
-        __syncwarp();
-        build_nodes<T>(sh, q, npan, 0, npan, dw, lane);
-        __syncwarp();
-        built = npan;
-      }
-      eval_panels<T>(sh, 0, npan, Bh, active, kr, ki, err);
-    } else {
-      for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
-        const int nb = min(kPanelBatch, npan - p0);
-        __syncwarp();
-        build_nodes<T>(sh, q, npan, p0, nb, dw, lane);
-        __syncwarp();
-        eval_panels<T>(sh, p0, nb, Bh, active, kr, ki, err);
-      }
-      built = 0;
-    }
-    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * est_sqrt(kr * kr + ki * ki));
-    ok = (!active) || err <= lim;
-    const bool any_bad = __any_sync(0xffffffffu, !ok);
-    if (!any_bad || refine >= q.max_refine || 2 * npan > max_panels) return cmake<C>(kr, ki);
-    ++refine;
-    npan *= 2;
-  }
-}
-
 template <typename T, typename C>
 __global__ void __launch_bounds__(256) wkernel_noalloc_kernel(const double* __restrict__ rho_in,
                                                               const double* __restrict__ dw_in,
@@ -1777,10 +1870,11 @@ __global__ void __launch_bounds__(256) wkernel_noalloc_kernel(const double* __re
     const double dw = dw_in[i];
     int built = 0;
     bool ok = true;
-    const C K = eval_chunk_capped<T, C>(
+    unsigned long long nodes = 0;
+    const C K = eval_chunk<T, C>(
         sh, q, rho, lane == 0, dw,
         initial_panels(q, static_cast<float>(rho), static_cast<float>(fabs(dw))), max_panels,
-        built, ok, lane);
+        built, ok, lane, nodes);
     if (lane == 0) {
       out[i] = K;
       if (!ok) atomicAdd(bad, 1ULL);
@@ -1856,6 +1950,7 @@ extern "C" int phi_wkernel_noalloc(const phi_wkernel_params* params, const doubl
   if (p.precision != PHI_F32 && p.precision != PHI_F64) return PHI_ERR_ARG;
   if (p.window_radius / p.du >= 1.0) return PHI_ERR_HORIZON;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (n_unconverged) PHI_TRY_NOT_CAPTURING(s);
   if (p.precision == PHI_F64)
     return phi::run_wkernel_noalloc<double, double2>(p, rho_dev, dw_dev, n,
                                                      static_cast<double2*>(k_dev), n_unconverged, s);

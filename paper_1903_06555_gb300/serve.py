@@ -27,6 +27,7 @@ completes; a resident plan keeps its measured size.
 """
 from __future__ import annotations
 
+import math
 import collections
 import concurrent.futures as cf
 import threading
@@ -88,7 +89,8 @@ def estimate_bytes(req: Request, planned: bool = False) -> int:
     m = int(req.uvw.shape[0])
     n = int(req.desc["image_n"])
     os_ = float(req.desc.get("oversample", 2.0))
-    npad = int(round(os_ * n))
+    # the library's lround: halves away from zero (Python's round() takes halves to even)
+    npad = int(math.floor(os_ * n + 0.5))
     f64 = req.desc.get("precision", "f32") == "f64"
     c = 16 if f64 else 8
     r = 8 if f64 else 4

@@ -1,4 +1,5 @@
-"""The device FP32 J0 (csrc/bessel_j0.cuh, Abramowitz & Stegun 9.4.1/9.4.3)
+"""The device FP32 J0 (csrc/bessel_j0.cuh: Abramowitz & Stegun 9.4.1 below x = 3,
+the modulus/phase form above, of degree 4 and, from x = 2 pi, of degree 2)
 compiled for the host and checked against scipy."""
 import os
 import subprocess
@@ -10,7 +11,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 CSRC = os.path.join(ROOT, "paper_1903_06555_gb300", "csrc")
 
 
-def host_j0(u):
+def host_j0(u, fn="j0_halfcycles"):
     code = r"""
 #include <cmath>
 #include <cstdio>
@@ -21,7 +22,7 @@ def host_j0(u):
 int main(int argc, char** argv) {
   FILE* f = fopen(argv[1], "rb"); FILE* g = fopen(argv[2], "wb");
   float u;
-  while (fread(&u, 4, 1, f) == 1) { float j = phi::j0_halfcycles(u); fwrite(&j, 4, 1, g); }
+  while (fread(&u, 4, 1, f) == 1) { float j = phi::FN(u); fwrite(&j, 4, 1, g); }
   fclose(f); fclose(g);
   return 0;
 }
@@ -29,8 +30,8 @@ int main(int argc, char** argv) {
     tmp = os.path.join(os.environ.get("TMPDIR", "/tmp"), f"phi_j0_{os.getpid()}")
     with open(tmp + ".cpp", "w") as f:
         f.write(code)
-    subprocess.run(["g++", "-O2", "-ffp-contract=off", "-I", CSRC, tmp + ".cpp", "-o", tmp],
-                   check=True)
+    subprocess.run(["g++", "-O2", "-ffp-contract=off", f"-DFN={fn}", "-I", CSRC, tmp + ".cpp",
+                    "-o", tmp], check=True)
     np.asarray(u, np.float32).tofile(tmp + ".in")
     subprocess.run([tmp, tmp + ".in", tmp + ".out"], check=True)
     out = np.fromfile(tmp + ".out", np.float32)
@@ -58,3 +59,19 @@ def test_j0_halfcycles_against_scipy():
     th = np.spacing(np.maximum(np.pi * u, 1.0).astype(np.float32)).astype(np.float64)
     rounding = env * np.sqrt((np.pi * ulp) ** 2 + th ** 2) / np.sqrt(24.0)
     assert np.sqrt(np.mean(err ** 2)) < 1.25 * np.hypot(1e-7, np.sqrt(np.mean(rounding ** 2)))
+
+
+def test_j0_far_against_scipy():
+    """The degree-2 form used for panels whose nodes all lie at u >= 2
+    (x >= 2 pi): the same bounds as the degree-4 form beyond x = 3."""
+    u = np.concatenate([np.linspace(2.0, 10.0, 40001), np.linspace(10.0, 130.0, 60001)]
+                       ).astype(np.float32)
+    got = host_j0(u, "j0_far").astype(np.float64)
+    ref = sp.j0(np.pi * u.astype(np.float64))
+    err = np.abs(got - ref)
+    env = np.sqrt(2.0 / (np.pi * np.pi * u))
+    ulp = np.spacing(u).astype(np.float64)
+    assert np.all(err <= 2e-7 + 2 * env * np.pi * ulp)
+    # and it agrees with the degree-4 form to the two fits' errors plus rounding
+    near = host_j0(u, "j0_large").astype(np.float64)
+    assert np.max(np.abs(near - got)) < 2e-7 + 4 * np.max(env * np.pi * ulp)

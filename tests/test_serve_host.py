@@ -40,3 +40,13 @@ def test_resident_plan_charges_inputs_and_outputs_only():
     assert S.estimate_bytes(r, planned=True) == io
     r64 = req(512, 8, m=20000, precision="f64")
     assert S.estimate_bytes(r64, planned=True) == 20000 * 2 * 16 + 512 * 512 * 2 * 8 + (16 << 20)
+
+
+def test_padded_grid_size_rounds_halves_up_like_the_library():
+    """The plan sizes its grid as lround(os * N), halves away from zero:
+    os = 2.5, N = 77 gives 192.5 -> 193 (Python's round() would give 192)."""
+    r = req(77, 1, oversample=2.5)
+    grid_193, grid_192 = 8 * 193 * 193, 8 * 192 * 192
+    base = S.estimate_bytes(req(77, 1, oversample=2.5 - 1e-9))   # 192.49... -> 192
+    # one stack: its grid, one batched-transform workspace grid, one more
+    assert S.estimate_bytes(r) - base == 3 * (grid_193 - grid_192)

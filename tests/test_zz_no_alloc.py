@@ -76,3 +76,21 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     rho = torch.zeros(4, dtype=torch.float64, device="cuda")
     st, _, _ = _raw_call(prm, rho, rho)
     assert st == phi.PHI_ERR_ARG
+
+
+def test_noalloc_counts_points_beyond_its_panel_cap():
+    """With max_panels = 2 the wide chirps of large |dw| cannot meet the
+    tolerance: the points are evaluated on the capped partition (finite
+    values) and counted; the Python wrapper and the raw C call agree."""
+    _, prm = _plan_and_params("f32")
+    prm.max_panels = 2
+    rng = np.random.default_rng(9)
+    rt = torch.from_numpy(rng.uniform(5, 20, 64)).cuda()
+    dt = torch.from_numpy(rng.uniform(200, 400, 64)).cuda()
+    st, raw, bad = _raw_call(prm, rt, dt)
+    assert st == phi.PHI_OK
+    assert 0 < bad <= 64
+    assert torch.isfinite(torch.view_as_real(raw)).all()
+    k, bad_w = phi.wkernel_noalloc(prm, rt, dt)
+    assert bad_w == bad
+    assert torch.equal(k, raw)
