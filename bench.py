@@ -41,7 +41,6 @@ FLOPS_PER_TAP_NODE = 36.0     # J0 by a rational/asymptotic approximation (28) +
 FP32_LANES_PER_SM = 128       # FP32 FMA lanes per SM per clock (Blackwell)
 RADIAL_POINTS = 16            # Chebyshev points per piece, FP32 radial mode
 RADIAL_FLOPS_PER_TAP = 96     # 15 Clenshaw steps x (2 FMA + 2 subtractions) + the last step
-NUM_SMS = 152
 
 
 def parse():
@@ -182,6 +181,17 @@ class ClockSampler:
                 "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
 
 
+def device_sms(dev=None):
+    """Streaming multiprocessors of the device, as the driver reports them."""
+    return torch.cuda.get_device_properties(dev if dev is not None else
+                                            torch.cuda.current_device()).multi_processor_count
+
+
+def fp32_peak_tflops(sms, sm_mhz):
+    """FP32 FMA peak: SMs x 128 FP32 lanes x 2 flops x clock."""
+    return sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -269,18 +279,17 @@ def workload_inputs(wl):
 
 # ---------------------------------------------------------------------------- reference arm
 
-def cpu_oracle_rate(wl, uvw, x, budget_s=20.0, tol=1e-6, accuracy=False):
+def cpu_oracle_rate(wl, uvw, x, budget_s=20.0, tol=1e-6, rate_tol12=False):
     """The FP64 oracle, as it stands, on the host cores: degrid of a bounded
     random sample of the workload's kept visibilities in chunks (per-stack
     grids built before the clock starts), gridding of the same sample in one
     call, plus one stack's image-domain steps (S~, pad, FFT forward; inverse
     FFT, crop, S~^H) and one padded-grid allocation timed once and charged
     K times.  Returns (vis/s projected to the full workload,
-    sampled visibilities, measured seconds, threads, accuracy), where
-    accuracy (with accuracy=True) holds the oracle at quadrature tol 1e-12 on
-    64 kept visibilities of the widest-support stack: their degrid values,
-    the image gridded from random values on them alone, and the projected
-    rate of that variant."""
+    sampled visibilities, measured seconds, threads, rate at tol 1e-12), the
+    last (with rate_tol12=True) the same projection for the oracle at the
+    parity tolerance 1e-12, timed on 64 kept visibilities of the
+    widest-support stack."""
     import oracle as O
     geo = O.geometry_from(wl, tol_rel=tol, tol_abs=tol)
     plan = O.make_plan(uvw, geo, wl.n_stacks, wl.conj_fold)
@@ -321,19 +330,15 @@ def cpu_oracle_rate(wl, uvw, x, budget_s=20.0, tol=1e-6, accuracy=False):
     t_used = t_deg + max(t_grid - len(stacks) * t_alloc, 0.0)
     t_full = t_used * (kept.size / n_done) + wl.n_stacks * (t_image + t_alloc)
     acc = None
-    if accuracy:
+    if rate_tol12:
         k = int(np.argmax([plan.jw[kept][plan.stack[kept] == s].max(initial=0)
                            for s in range(wl.n_stacks)]))
         sel = np.sort(order[plan.stack[order] == k][:64])
         t0 = time.perf_counter()
-        y_ref, _, _ = O.degrid_from_grids(plan, grids, sel, 1e-12, 1e-12)
-        g_acc, _, _ = O.grid_to_stacks(plan, y[sel], sel, 1e-12, 1e-12)
+        O.degrid_from_grids(plan, grids, sel, 1e-12, 1e-12)
+        O.grid_to_stacks(plan, y[sel], sel, 1e-12, 1e-12)
         t12 = max(time.perf_counter() - t0 - t_alloc, 1e-9)   # one stack's grid allocation
-        img_ref = O.image_from_grids(plan, g_acc)
-        acc = {"sel": sel, "y_ref": y_ref, "y_in": y[sel], "img_ref": img_ref, "stack": k,
-               "jw": int(plan.jw[sel[0]]),
-               "rate_tol1e-12": kept.size / (t12 * kept.size / sel.size +
-                                             wl.n_stacks * (t_image + t_alloc))}
+        acc = kept.size / (t12 * kept.size / sel.size + wl.n_stacks * (t_image + t_alloc))
     return kept.size / t_full, n_done, t_deg + t_grid + t_image, threads, acc
 
 
@@ -468,7 +473,8 @@ def run_ours(args, ws, rank, local):
     achieved = flops_step / launches_per_step / ((ms_dom / n_dom) / 1e3) / 1e12
     peaks = measured_peaks()
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
-    peak_fp32 = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    sms = device_sms(dev)
+    peak_fp32 = fp32_peak_tflops(sms, sm_mhz)
     clocks = clk.summary()
     if args.kernel_mode == "table":
         # HBM bytes one launch (all stacks of the resident group) must move at
@@ -498,7 +504,7 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "kernel": f"vis_radial_kernel ({dom})", "achieved": ach,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32,
                 "traffic": profiled_traffic("radial_" + dom),
-                "peak_note": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
+                "peak_note": f"FP32 FMA: {sms} SMs (device count) x {FP32_LANES_PER_SM} lanes x 2 flops x "
                              f"{sm_mhz:.0f} MHz (recipe unit counts, max clock)",
                 "work_note": f"{FLOPS_PER_TAP_NODE:.0f} flops per quadrature tap-node at the "
                              f"Chebyshev points + {RADIAL_FLOPS_PER_TAP} flops per tap for its "
@@ -507,7 +513,7 @@ def run_ours(args, ws, rank, local):
         roof = {"bound": "alu", "kernel": f"vis_kernel ({dom})", "achieved": achieved,
                 "peak": peak_fp32, "unit": "TFLOP/s", "frac": achieved / peak_fp32,
                 "traffic": profiled_traffic(dom),
-                "peak_note": f"FP32 FMA: {NUM_SMS} SMs x {FP32_LANES_PER_SM} lanes x 2 flops x "
+                "peak_note": f"FP32 FMA: {sms} SMs (device count) x {FP32_LANES_PER_SM} lanes x 2 flops x "
                              f"{sm_mhz:.0f} MHz (recipe unit counts, max clock)",
                 "work_note": f"{FLOPS_PER_TAP_NODE:.0f} flops per tap-node x oracle tap-nodes "
                              f"per visibility at tol 1e-6"}
@@ -557,35 +563,69 @@ def run_ours(args, ws, rank, local):
         "wall_s_timed": wall,
     }
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
-        rate, n, t, threads, acc = cpu_oracle_rate(wl, uvw_np, x_np, budget_s=20.0,
-                                                   accuracy=not args.max_vis)
+        rate, n, t, threads, rate12 = cpu_oracle_rate(wl, uvw_np, x_np, budget_s=20.0,
+                                                      rate_tol12=not args.max_vis)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{n} random kept visibilities of the workload, degrid+grid, "
                                           f"FP64 oracle at quadrature tol 1e-6, plus one stack's "
                                           f"image-domain steps charged per stack ({t:.1f} s "
                                           "measured); projected to the full workload"}
-        if acc is not None:
-            line["cpu_baseline"]["value_tol1e-12"] = acc["rate_tol1e-12"]
-            # the error of this run's FP32 results against the FP64 oracle at
-            # quadrature tol 1e-12: degrid values of the sampled visibilities,
-            # and the image gridded from values on those visibilities alone
-            sel = acc["sel"]
-            y32 = plan.degrid(x).cpu().numpy().astype(np.complex128)
-            ym = np.zeros(M, np.complex64)
-            ym[sel] = acc["y_in"]
-            img32 = plan.grid(torch.from_numpy(ym).to(dev)).cpu().numpy().astype(np.float64)
-
-            def rel(a, b):
-                return float(np.linalg.norm(a - b) / np.linalg.norm(b))
-            line["accuracy_vs_fp64_oracle"] = {
-                "degrid_rel_l2": rel(y32[sel], acc["y_ref"]),
-                "grid_rel_l2": rel(img32, acc["img_ref"]),
-                "bound": 1e-5,
-                "sample": f"{sel.size} kept visibilities of stack {acc['stack']} (J_w = {acc['jw']}, "
-                          "the widest support), oracle at quadrature tol 1e-12"}
+        if rate12 is not None:
+            line["cpu_baseline"]["value_tol1e-12"] = rate12
+        if not args.max_vis:
+            line["accuracy_vs_fp64_oracle"] = accuracy_vs_oracle(plan, x, uvw_np, wl, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
+
+
+def accuracy_vs_oracle(plan, x, uvw_np, wl, dev):
+    """This run's FP32 results (the full plan, the timed launch configuration)
+    against the FP64 oracle at quadrature tolerance 1e-12, from
+    tests/golden/mwa_dense_cells.npz (written from oracle/ alone by
+    tests/golden/make_dense_cells.py): degrid values of 2,000 kept
+    visibilities, 250 per stack; and, per stack, the image gridded from a
+    visibility vector that is zero except on the visibilities covering that
+    stack's busiest grid cell, which they fill to its full-run density
+    (960 to 2,552 contributions), then all stacks together."""
+    import oracle as O
+    g = np.load(os.path.join(ROOT, "tests", "golden", "mwa_dense_cells.npz"))
+    geo = O.geometry_from(wl, tol_rel=1e-12, tol_abs=1e-12)
+    full = O.make_plan(uvw_np, geo, wl.n_stacks, wl.conj_fold)
+    M = len(uvw_np)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    y32 = plan.degrid(x).cpu().numpy().astype(np.complex128)
+    s = g["sample_sel"]
+    deg = [rel(y32[s][full.stack[s] == k], g["sample_y_ref"][full.stack[s] == k])
+           for k in range(wl.n_stacks)]
+    sel = g["dense_sel"]
+    y_in = W.random_vis(M, int(g["vis_seed"]))
+    grid_k, img_sum, ref_sum = [], 0.0, 0.0
+    for k in range(wl.n_stacks):
+        pick = sel[full.stack[sel] == k]
+        ym = np.zeros(M, np.complex64)
+        ym[pick] = y_in[pick]
+        img = plan.grid(torch.from_numpy(ym).to(dev)).cpu().numpy().astype(np.float64)
+        J = int(g["stack_jw"][k])
+        v0, u0 = (int(t) for t in g[f"dense_patch_origin_{k}"])
+        grid = np.zeros((geo.Npad, geo.Npad), np.complex128)
+        grid[np.ix_(np.arange(v0, v0 + 2 * J - 1) % geo.Npad,
+                    np.arange(u0, u0 + 2 * J - 1) % geo.Npad)] = g[f"dense_patch_{k}"]
+        ref = O.image_from_grids(full, {k: grid})
+        grid_k.append(rel(img, ref))
+        img_sum = img_sum + img
+        ref_sum = ref_sum + ref
+    return {"degrid_rel_l2": rel(y32[s], g["sample_y_ref"]), "degrid_rel_l2_max_stack": max(deg),
+            "degrid_rel_l2_per_stack": deg,
+            "grid_rel_l2": rel(img_sum, ref_sum), "grid_rel_l2_max_stack": max(grid_k),
+            "grid_rel_l2_per_stack": grid_k, "bound": 1e-5,
+            "sample": f"degrid: {s.size} kept visibilities, {s.size // wl.n_stacks} per stack; "
+                      f"grid: {sel.size} visibilities covering each stack's busiest cell "
+                      f"({int(g['dense_count'].min())}-{int(g['dense_count'].max())} "
+                      "contributions, the full-run count); oracle at quadrature tol 1e-12 "
+                      "(tests/golden/mwa_dense_cells.npz)"}
 
 
 def run_e2e(phi, desc, uvw_np, x_np, steps, dev):
@@ -984,7 +1024,7 @@ def run_dde(args):
     flops = (nodes * FLOPS_PER_TAP_NODE + taps * (jd * jd + jd) * 8.0) / calls
     ach = flops / (ms_dde / 2 / 1e3) / 1e12
     peaks = measured_peaks()
-    peak_fp32 = NUM_SMS * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    peak_fp32 = fp32_peak_tflops(device_sms(), peaks.get("sm_max_mhz", 2070.0))
     line = {"metric": "w-corrected visibilities/s with a DDE per visibility (degrid+grid)",
             "value": n_kept / (ms_dde / 1e3), "unit": UNIT,
             "workload": f"{wl.name} without the fold: 16 stacks (J_w up to {info['max_jw']}), "

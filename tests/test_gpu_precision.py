@@ -3,6 +3,7 @@ FP64 oracle, on the precision-study workload (4096^2 image, 8192^2 grid,
 17.5M visibilities, |w| <= 1500, 32 stacks, fold on) and on plans with given
 centres (phi_plan_create_fixed)."""
 import math
+import os
 
 import numpy as np
 import pytest
@@ -77,3 +78,49 @@ def test_precision_study_fp32_vs_fp64_and_oracle(precision_workload):
     ref = O.degrid(op, x, subset=pick)
     assert O.rel_l2(s64[pick], ref) < 1e-10
     assert O.rel_l2(s32[pick], ref) < 1e-5
+
+
+def test_fp32_error_estimate_decides_like_fp64():
+    """The adaptive quadrature's accept/refine decisions (Sec. 4 tolerance
+    1e-6) taken from the FP32 error estimate equal those of the FP64 path.
+
+    Both precisions start every chunk of taps from the same a-priori panel
+    count (computed in FP32 from the same inputs) and double it while any
+    tap's estimate exceeds max(abs_tol, rel_tol |K|); the FP64 path forms
+    the estimate from FP64 node values, J0 and sums.  Equal tap-node totals
+    over the same visibilities therefore mean that no chunk was refined by
+    one precision and accepted by the other; the difference bounds how many
+    were.  Either way the result stays within the tolerance: a refined chunk
+    is only more accurate.  Workload: 4,000 kept
+    visibilities of the MWA-like snapshot (all 8 stacks, J_w 26-36), degrid
+    and grid, with the full plan's centres and supports."""
+    g = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                             "mwa_dense_cells.npz"))
+    wl = W.mwa_snapshot()
+    uvw = W.uvw_for(wl)
+    sel = W.subsample(len(uvw), 4000, 17)
+    sub = torch.from_numpy(np.ascontiguousarray(uvw[sel]))
+    kw = dict(image_n=wl.image_n, fov_rad=math.radians(wl.fov_deg), n_stacks=wl.n_stacks,
+              conj_fold=int(wl.conj_fold), centres=g["centres"], stack_jw=g["stack_jw"],
+              quad_rel_tol=1e-6, quad_abs_tol=1e-6)
+    x = W.point_sources(wl.image_n, wl.n_sources, wl.seed)
+    y = W.random_vis(len(sel), 3)
+    counts = {}
+    for prec, rd, cd in (("f32", torch.float32, torch.complex64),
+                         ("f64", torch.float64, torch.complex128)):
+        plan = phi.Plan(sub, precision=prec, **kw)
+        plan.degrid(torch.from_numpy(x).cuda().to(rd))
+        plan.grid(torch.from_numpy(y).cuda().to(cd))
+        counts[prec] = plan.stats_full()
+        plan.close()
+    print("FP32 (unconverged, taps, tap-nodes):", counts["f32"], " FP64:", counts["f64"])
+    assert counts["f32"][1] == counts["f64"][1] > 0
+    assert counts["f32"][0] == counts["f64"][0] == 0
+    # The FP32 panel sums carry rounding of order 2^-24 sum_j |w_j h_j J_j|
+    # (~6e-8 summed over the panels, against the 1e-6 tolerance), so a chunk
+    # whose estimate lies within a few percent of the limit can be refined by
+    # one precision only: measured 2.6e-4 of the tap-nodes on this workload
+    # (about 55 of ~240,000 chunk decisions), FP32 the one refining more.  One
+    # differing decision moves ~15 npan x 32 tap-nodes (~5e-6 of the total);
+    # the bound allows about 200.
+    assert abs(counts["f32"][2] - counts["f64"][2]) <= 1e-3 * counts["f64"][2]
