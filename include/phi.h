@@ -38,9 +38,9 @@
  *     when the visibility was folded.  Visibilities whose own u/du or v/du lie
  *     outside [-Npad/2, Npad/2) are dropped: y_i = 0, and they add nothing to
  *     the adjoint.
- *   - Quadrature acceptance per tap: sum over panels |K15 - G7| <=
- *     max(quad_abs_tol, quad_rel_tol * |K|) (paper: 1e-6 relative and absolute,
- *     Sec. 4).  Taps that do not converge within the refinement cap are
+ *   - Quadrature: Gauss-Kronrod 15/31 on equal panels of [0, R].  Acceptance
+ *     per tap: sum over panels |K31 - G15| <= max(quad_abs_tol,
+ *     quad_rel_tol * |K|) (paper: 1e-6 relative and absolute, Sec. 4).  Taps that do not converge within the refinement cap are
  *     counted (phi_plan_stats), never an error.
  *
  * Memory and streams: every pointer argument named *_dev is a device pointer
@@ -81,8 +81,8 @@ enum phi_status {
 };
 
 enum phi_precision {
-  PHI_F32 = 0,  /* FP32 grid, FFT, kernel and accumulation; FP64 chirp phase
-                   argument and FP64 quadrature error accumulation           */
+  PHI_F32 = 0,  /* FP32 grid, FFT, kernel, accumulation and quadrature error
+                   estimate; FP64 chirp phase argument                       */
   PHI_F64 = 1   /* everything in FP64                                        */
 };
 
@@ -116,13 +116,19 @@ typedef struct {
                                processed together (0: 4096 MiB); at least
                                one grid is always held                      */
   int32_t kernel_mode;      /* enum phi_kernel_mode                          */
-  int32_t grid_staging;     /* PHI_KERNEL_TABLE only: 1 = one thread block per
-                               uv tile with its grid patch (tile + J_w cells
-                               a side) staged in shared memory, gridding
-                               privatised there and added to the grid once
-                               per tile; 0 = one warp per visibility reading
-                               the grid directly (default; as fast or faster
-                               on the workloads measured) */
+  int32_t grid_staging;     /* PHI_KERNEL_TABLE only: 0 = one warp per
+                               visibility, table and grid read directly
+                               (default); 1 = one thread block per uv tile
+                               with its grid patch (tile + J_w cells a side)
+                               staged in shared memory, gridding privatised
+                               there and added to the grid once per tile;
+                               2 = one thread block per w-row of the table:
+                               the pair of w-planes around that row staged
+                               in shared memory once for every visibility
+                               whose |dw| falls on it (the plan keeps an
+                               index of the records sorted by stack and
+                               w-row; falls back to 0 when a row exceeds a
+                               block's shared memory) */
   int32_t reserved0;        /* must be 0                                     */
   double oversample;        /* os; Npad = os * N must be an even integer     */
   double fov_rad;           /* full field of view in direction cosine        */
@@ -316,7 +322,7 @@ int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, in
  * phi_wkernel_noalloc evaluates [GC](rho_i, dw_i) like phi_wkernel, with the
  * same device routine, but without a plan and without allocating: its
  * scratch (the quadrature node tables and one counter) lives in a fixed
- * file-scope device array of PHI_WKERNEL_NOALLOC_SCRATCH_BYTES (about 732
+ * file-scope device array of PHI_WKERNEL_NOALLOC_SCRATCH_BYTES (about 384
  * KiB), which every GPU that loads the library holds until the process
  * exits.  The caller passes the inputs and outputs.
  *
@@ -335,8 +341,8 @@ int phi_wkernel(phi_plan_t plan, const double* rho_dev, const double* dw_dev, in
  * the GPU (different streams, or host threads racing) race on it and must be
  * serialised by the caller.
  */
-#define PHI_WKERNEL_NOALLOC_MAX_PANELS 64
-#define PHI_WKERNEL_NOALLOC_SCRATCH_BYTES (256 + 3 * 8 * (15 * 64 * 65 / 2))
+#define PHI_WKERNEL_NOALLOC_MAX_PANELS 32
+#define PHI_WKERNEL_NOALLOC_SCRATCH_BYTES (256 + 3 * 8 * (31 * 32 * 33 / 2))
 
 typedef struct {
   double du;                /* grid spacing in wavelengths (phi_plan_info du)   */

@@ -108,7 +108,7 @@ class WKernelParams(ctypes.Structure):
     ]
 
 
-WKERNEL_NOALLOC_MAX_PANELS = 64
+WKERNEL_NOALLOC_MAX_PANELS = 32
 
 _LIB = None
 _LOCK = threading.Lock()

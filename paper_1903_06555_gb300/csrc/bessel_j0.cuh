@@ -7,7 +7,8 @@
 // as degree-4 polynomials in 1/u^2 (the parities of their Hankel expansions,
 // A&S 9.2.28-9.2.31), coefficients fitted by j0_fit.py in this directory
 // (|error| < 5.2e-8); for u >= 2 the same form with both polynomials of
-// degree 2 (|error| < 4.7e-8, two multiply-adds fewer per polynomial).
+// degree 2 (|error| < 4.7e-8, two multiply-adds fewer per polynomial), and
+// for u >= 4.5 of degree 1 (|error| < 4.9e-8).
 // The phase theta0 = pi (u + D/u) - pi/4 is formed in FP32 and handed to the
 // hardware cosine, which reduces it by whole turns itself.  The argument's own
 // FP32 rounding (relative 6e-8, i.e. 6e-6 rad at 100 rad, the largest phase a
@@ -116,11 +117,26 @@ PHI_HD inline float j0_far(float u) {
   return (r * f) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
 }
 
+// Lower end of the degree-1 form: u = 4.5.
+constexpr float kJ0Farthest = 4.5f;
+
+// J0(pi u) for u >= kJ0Farthest: the same form with F and D of degree 1 (the
+// fit of j0_fit.py on [4.5, 1e5]; J0 error <= 4.5e-8 from F, 3.6e-9 from D).
+PHI_HD inline float j0_farthest(float u) {
+  const float r = j0_rsqrt(u);
+  const float s = r * r;
+  const float q = s * s;
+  const float f = j0_fma(-2.824241012e-03f, q, 4.501578963e-01f);
+  const float d = j0_fma(6.546436681e-04f, q, -1.266495887e-02f);
+  const float phi = j0_fma(d, s, u);
+  return (r * f) * j0_cos(j0_fma(phi, 3.14159265358979f, -0.785398163397448f));
+}
+
 #if defined(__CUDACC__)
 // Two arguments at once in Blackwell's paired FP32 arithmetic (f32x2 FMA
 // and multiply, one instruction for both halves): the same operations, in
-// the same order and rounding, as j0_small, j0_large and j0_far on each
-// half.
+// the same order and rounding, as j0_small, j0_large, j0_far and
+// j0_farthest on each half.
 __device__ __forceinline__ float2 j0_pair(float a, float b) { return make_float2(a, b); }
 
 __device__ __forceinline__ float2 j0_small2(float2 u) {
@@ -148,6 +164,20 @@ __device__ __forceinline__ float2 j0_large2(float2 u) {
   d = __ffma2_rn(d, q, j0_pair(-1.853455306e-04f, -1.853455306e-04f));
   d = __ffma2_rn(d, q, j0_pair(6.629692300e-04f, 6.629692300e-04f));
   d = __ffma2_rn(d, q, j0_pair(-1.266485270e-02f, -1.266485270e-02f));
+  const float2 phi = __ffma2_rn(d, s, u);
+  const float2 th = __ffma2_rn(phi, j0_pair(3.14159265358979f, 3.14159265358979f),
+                               j0_pair(-0.785398163397448f, -0.785398163397448f));
+  return __fmul2_rn(__fmul2_rn(r, f), j0_pair(j0_cos(th.x), j0_cos(th.y)));
+}
+
+__device__ __forceinline__ float2 j0_farthest2(float2 u) {
+  const float2 r = j0_pair(j0_rsqrt(u.x), j0_rsqrt(u.y));
+  const float2 s = __fmul2_rn(r, r);
+  const float2 q = __fmul2_rn(s, s);
+  const float2 f = __ffma2_rn(j0_pair(-2.824241012e-03f, -2.824241012e-03f), q,
+                              j0_pair(4.501578963e-01f, 4.501578963e-01f));
+  const float2 d = __ffma2_rn(j0_pair(6.546436681e-04f, 6.546436681e-04f), q,
+                              j0_pair(-1.266495887e-02f, -1.266495887e-02f));
   const float2 phi = __ffma2_rn(d, s, u);
   const float2 th = __ffma2_rn(phi, j0_pair(3.14159265358979f, 3.14159265358979f),
                                j0_pair(-0.785398163397448f, -0.785398163397448f));

@@ -8,9 +8,9 @@ polynomials in q = 1/u^2:
 
     J0(pi u) = u^{-1/2} F(q) cos(pi (u + D(q) / u) - pi/4),
 
-F and D of degree 4 in q for u >= 3/pi, and of degree 2 for u >= 2 (x >= 2 pi),
-where the Hankel series converge fast enough that the lower degree keeps the
-same accuracy.  The coefficients minimise the largest absolute error of J0
+F and D of degree 4 in q for u >= 3/pi, of degree 2 for u >= 2 (x >= 2 pi)
+and of degree 1 for u >= 4.5, where the Hankel series converge fast enough
+that the lower degrees keep the same accuracy.  The coefficients minimise the largest absolute error of J0
 this form gives (the L-infinity fit, solved as a linear program on a dense
 grid of u in [u_min, 1e5]), separately for the modulus and the phase part,
 against scipy's j0 and y0.  Run it to print the constants of both fits.
@@ -23,6 +23,8 @@ U_MIN = 3.0 / np.pi
 DEGREE = 4
 U_MIN_FAR = 2.0
 DEGREE_FAR = 2
+U_MIN_FARTHEST = 4.5
+DEGREE_FARTHEST = 1
 
 
 def modulus_and_phase(u):
@@ -78,7 +80,8 @@ def max_errors(cf, cd, n=300001, u_min=U_MIN):
 
 
 if __name__ == "__main__":
-    for u_min, degree in ((U_MIN, DEGREE), (U_MIN_FAR, DEGREE_FAR)):
+    for u_min, degree in ((U_MIN, DEGREE), (U_MIN_FAR, DEGREE_FAR),
+                          (U_MIN_FARTHEST, DEGREE_FARTHEST)):
         cf, cd = fit(u_min=u_min, degree=degree)
         ef, ed = max_errors(cf, cd, u_min=u_min)
         print(f"// u >= {u_min:.6f}, degree {degree}: max |J0 error| from the modulus "

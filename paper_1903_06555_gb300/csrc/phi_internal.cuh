@@ -8,9 +8,10 @@
 //   perm[n_kept]        caller index of each sorted record, bit 31 = folded;
 //   omn_pix[N*N]        1 - n(l, m) per pixel (FP64, for the chirp phase);
 //   corr_pix[N*N]       1 / (g(du |l|) n(l, m)) per pixel (precision T);
-//   node tables         per panel count P = 1..192: 1 - n(r_j) (FP64) and
-//                       w 2 pi h g(r_j) r_j (T, Kronrod and Kronrod-minus-
-//                       Gauss weights w) at the 15 P Gauss-Kronrod nodes;
+//   node tables         per panel count P = 1..128: 1 - n(r_j) (FP64) and
+//                       w 2 pi h g(r_j) r_j (T: the Kronrod weight, and the
+//                       Gauss weight in FP32 or the Kronrod-minus-Gauss
+//                       weight in FP64) at the 31 P Gauss-Kronrod nodes;
 //   tap order           per even support J_w, its J_w^2 taps sorted by
 //                       distance from the box centre (uint16 a | b << 8);
 //   grids               padded complex grids of one group of stacks at a
@@ -33,11 +34,12 @@ namespace phi {
 constexpr double kPi = 3.14159265358979323846264338327950288;
 constexpr float kPiF = 3.14159265358979323846f;
 
-// Panel counts 1..kMaxPanels; the node tables hold every partition
-// (panel count P at offset 15 P (P - 1) / 2).
-constexpr int kMaxPanels = 192;
+// Gauss-Kronrod 15/31 nodes per panel; panel counts 1..kMaxPanels, the node
+// tables holding every partition (panel count P at offset 31 P (P - 1) / 2).
+constexpr int kNodesPerPanel = 31;
+constexpr int kMaxPanels = 128;
 __host__ __device__ inline int64_t panel_table_offset(int npan) {
-  return 15 * static_cast<int64_t>(npan) * (npan - 1) / 2;
+  return kNodesPerPanel * static_cast<int64_t>(npan) * (npan - 1) / 2;
 }
 __host__ __device__ inline int panel_count_for(float want) {
   // want may be NaN or huge: clamp without relying on the conversion
@@ -46,12 +48,14 @@ __host__ __device__ inline int panel_count_for(float want) {
   return static_cast<int>(ceilf(want));
 }
 
-// Largest number of visibility records in one uv-tile work item.
+// Largest number of visibility records in one uv-tile work item, and in one
+// w-row work item of the table path's row staging.
 constexpr int kItemRecords = 128;
+constexpr int kRowItemRecords = 1024;
 
 // Panels evaluated per batch out of the per-warp shared node buffer.
-constexpr int kPanelBatch = 16;
-constexpr int kNodeBatch = 15 * kPanelBatch;
+constexpr int kPanelBatch = 8;
+constexpr int kNodeBatch = kNodesPerPanel * kPanelBatch;
 
 template <typename T> struct Cplx;
 template <> struct Cplx<float> { typedef float2 type; };
@@ -116,7 +120,7 @@ struct QuadParams {
   int npad;
   const double* node_omn;  // 1 - n(r_j) per node, all panel counts
   const void* node_hk;     // w_K(j) 2 pi h g(r_j) r_j per node (T)
-  const void* node_hd;     // (w_K(j) - w_G(j)) 2 pi h g(r_j) r_j per node (T)
+  const void* node_hd;     // w_G(j) (FP32) or w_K(j) - w_G(j) (FP64), times 2 pi h g(r_j) r_j
   const uint16_t* tap_order;  // per even J_w: taps (a | b << 8) by distance from the box centre
   const int32_t* tap_off;     // offset of the list for J_w = 2 i + 2 at index i
 };
@@ -170,11 +174,15 @@ struct Plan {
   int64_t table_nr = 0, table_nw = 0;
   double table_hr = 0, table_hw = 0;
   std::vector<double> stack_maxabs;   // largest |w - wbar_k| of each stack's kept visibilities
-  // uv-tile work items (table path): item i covers sorted records
-  // [item_start[2 i], item_start[2 i + 1]), all in the uv tile item_key[i]
-  // (low 24 bits: tile_v * tiles_per_row + tile_u), at most kItemRecords
+  // work items of the table path's staged kernels.  grid_staging 1: item i
+  // covers sorted records [item_start[2 i], item_start[2 i + 1]), all in the
+  // uv tile item_key[i] (low 24 bits: tile_v * tiles_per_row + tile_u), at
+  // most kItemRecords; grid_staging 2: the records row_idx[item_start[2 i]
+  // .. item_start[2 i + 1]), all on w-row item_key[i] (low 24 bits), at most
+  // kRowItemRecords; the top 8 bits of a key hold the stack
   int32_t* item_start = nullptr;
   uint32_t* item_key = nullptr;
+  uint32_t* row_idx = nullptr;          // kept records sorted by (stack, w-row)
   std::vector<int64_t> stack_item_off;  // K + 1 offsets into the items
   std::vector<uint8_t> stack_staged;    // table path: stage this stack's grid tiles
   int tile = 32;

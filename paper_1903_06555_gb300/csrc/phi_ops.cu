@@ -9,11 +9,12 @@
 // Kernel evaluation.  One warp owns one visibility.  The chirp part of the
 // integrand, h(r_j) = 2 pi h_p g(r_j) r_j e^{-2 pi i dw (n(r_j) - 1)}, is the
 // same for all J_w^2 taps of the visibility, so the lanes first build it at
-// the Gauss-Kronrod nodes of an a-priori panel partition of [0, R] (FP64
-// phase argument, tabulated 1 - n(r_j) and g(r_j)), then each lane takes one
-// tap and sums J0(2 pi rho r_j) h(r_j) with the Kronrod weights, and the
-// difference against the embedded Gauss rule as the error estimate (summed
-// over panels in FP64).  A chunk of 32 taps whose estimate misses
+// the Gauss-Kronrod 15/31 nodes of an a-priori partition of [0, R] into
+// equal panels (FP64 phase argument, tabulated 1 - n(r_j) and g(r_j)), then
+// each lane takes one tap and sums J0(2 pi rho r_j) h(r_j) with the Kronrod
+// weights, and, per panel, the difference against the embedded Gauss rule
+// as the error estimate (FP32 path: in paired f32x2 arithmetic, two nodes
+// per instruction).  A chunk of 32 taps whose estimate misses
 // max(abs_tol, rel_tol |K|) is recomputed with twice the panels (up to
 // max_refine times); taps still above tolerance are counted.  The degridder
 // and the gridder run this identical routine, so [GC] and its conjugate
@@ -22,6 +23,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "bessel_j0.cuh"
 #include "table_index.cuh"
@@ -30,39 +32,65 @@
 namespace phi {
 
 // ---------------------------------------------------------------------------
-// Gauss-Kronrod 7/15 rule on [-1, 1] (published constants of QUADPACK's
-// qk15, Piessens et al. 1983).  Node j = 0..14 runs from -1 to 1.
+// Gauss-Kronrod 15/31 rule on [-1, 1]: the 15-point Gauss-Legendre rule and
+// its Kronrod extension (the zeros of the Stieltjes polynomial E_16), as
+// computed by gk_rule.py in this directory from the rule's definition.
+// Node j = 0..30 runs from -1 to 1; i = 0..15 indexes |x| from the outermost
+// node to the centre.  The Gauss nodes are the odd j (i odd, and the centre).
 // ---------------------------------------------------------------------------
+constexpr int kNodes = kNodesPerPanel;   // 31
 __host__ __device__ constexpr double gk_abs_node(int i) {
-  return i == 0 ? 0.991455371120812639206854697526329
-       : i == 1 ? 0.949107912342758524526189684047851
-       : i == 2 ? 0.864864423359769072789712788640926
-       : i == 3 ? 0.741531185599394439863864773280788
-       : i == 4 ? 0.586087235467691130294144845693013
-       : i == 5 ? 0.405845151377397166906606412076961
-       : i == 6 ? 0.207784955007898467600689403773245
+  return i == 0 ? 0.998002298693397060285172840152271209
+       : i == 1 ? 0.987992518020485428489565718586612581
+       : i == 2 ? 0.967739075679139134257347978784337225
+       : i == 3 ? 0.937273392400705904307758947710209471
+       : i == 4 ? 0.897264532344081900882509656454495883
+       : i == 5 ? 0.848206583410427216200648320774216851
+       : i == 6 ? 0.790418501442465932967649294817947347
+       : i == 7 ? 0.72441773136017004741618605461393801
+       : i == 8 ? 0.650996741297416970533735895313274693
+       : i == 9 ? 0.570972172608538847537226737253910641
+       : i == 10 ? 0.485081863640239680693655740232350613
+       : i == 11 ? 0.394151347077563369897207370981045468
+       : i == 12 ? 0.299180007153168812166780024266388963
+       : i == 13 ? 0.201194093997434522300628303394596208
+       : i == 14 ? 0.101142066918717499027074231447392339
+       : i == 15 ? 0.0
                 : 0.0;
 }
 __host__ __device__ constexpr double gk_kronrod_weight(int i) {
-  return i == 0 ? 0.022935322010529224963732008058970
-       : i == 1 ? 0.063092092629978553290700663189204
-       : i == 2 ? 0.104790010322250183839876322541518
-       : i == 3 ? 0.140653259715525918745189590510238
-       : i == 4 ? 0.169004726639267902826583426598550
-       : i == 5 ? 0.190350578064785409913256402421014
-       : i == 6 ? 0.204432940075298892414161999234649
-                : 0.209482141084727828012999174891714;
-}
-__host__ __device__ constexpr double gk_gauss_weight(int i) {  // at gk_abs_node(i), odd i
-  return i == 1 ? 0.129484966168869693270611432679082
-       : i == 3 ? 0.279705391489276667901467771423780
-       : i == 5 ? 0.381830050505118944950369775488975
-       : i == 7 ? 0.417959183673469387755102040816327
+  return i == 0 ? 0.00537747987292334898779205143012764982
+       : i == 1 ? 0.0150079473293161225383747630758072681
+       : i == 2 ? 0.0254608473267153201868740010196533594
+       : i == 3 ? 0.0353463607913758462220379484783600481
+       : i == 4 ? 0.0445897513247648766082272993732796902
+       : i == 5 ? 0.0534815246909280872653431472394302968
+       : i == 6 ? 0.0620095678006706402851392309608029322
+       : i == 7 ? 0.0698541213187282587095200770991474758
+       : i == 8 ? 0.0768496807577203788944327774826590067
+       : i == 9 ? 0.0830805028231330210382892472861037896
+       : i == 10 ? 0.0885644430562117706472754436937743032
+       : i == 11 ? 0.0931265981708253212254868727473457186
+       : i == 12 ? 0.0966427269836236785051799076275893351
+       : i == 13 ? 0.0991735987217919593323931734846031311
+       : i == 14 ? 0.100769845523875595044946662617569722
+       : i == 15 ? 0.101330007014791549017374792767492547
                 : 0.0;
 }
-__host__ __device__ constexpr int gk_fold(int j) { return j < 7 ? j : 14 - j; }
+__host__ __device__ constexpr double gk_gauss_weight(int i) {  // at gk_abs_node(i), 0 for Kronrod-only
+  return i == 1 ? 0.0307532419961172683546283935772044177
+       : i == 3 ? 0.0703660474881081247092674164506673385
+       : i == 5 ? 0.107159220467171935011869546685869303
+       : i == 7 ? 0.139570677926154314447804794511028323
+       : i == 9 ? 0.166269205816993933553200860481208811
+       : i == 11 ? 0.186161000015562211026800561866422825
+       : i == 13 ? 0.198431485327111576456118326443839325
+       : i == 15 ? 0.202578241925561272880620199967519315
+                : 0.0;
+}
+__host__ __device__ constexpr int gk_fold(int j) { return j < 15 ? j : 30 - j; }
 __host__ __device__ constexpr double gk_node(int j) {
-  return j < 7 ? -gk_abs_node(j) : gk_abs_node(14 - j);
+  return j < 15 ? -gk_abs_node(j) : gk_abs_node(30 - j);
 }
 __host__ __device__ constexpr double gk_wk(int j) { return gk_kronrod_weight(gk_fold(j)); }
 __host__ __device__ constexpr double gk_wd(int j) {  // Kronrod minus Gauss weight
@@ -73,20 +101,32 @@ __host__ __device__ constexpr double gk_gw(int j) {  // Gauss weight (0: Kronrod
 }
 
 // Nodes in the precision of the integrand, read uniformly by the whole warp.
-__constant__ float c_gk_node_f[15] = {
-    -0.991455371120812639f, -0.949107912342758525f, -0.864864423359769073f,
-    -0.741531185599394440f, -0.586087235467691130f, -0.405845151377397167f,
-    -0.207784955007898468f, 0.0f, 0.207784955007898468f, 0.405845151377397167f,
-    0.586087235467691130f, 0.741531185599394440f, 0.864864423359769073f,
-    0.949107912342758525f, 0.991455371120812639f};
-__constant__ double c_gk_node_d[15] = {
-    -0.991455371120812639206854697526329, -0.949107912342758524526189684047851,
-    -0.864864423359769072789712788640926, -0.741531185599394439863864773280788,
-    -0.586087235467691130294144845693013, -0.405845151377397166906606412076961,
-    -0.207784955007898467600689403773245, 0.0, 0.207784955007898467600689403773245,
-    0.405845151377397166906606412076961, 0.586087235467691130294144845693013,
-    0.741531185599394439863864773280788, 0.864864423359769072789712788640926,
-    0.949107912342758524526189684047851, 0.991455371120812639206854697526329};
+__constant__ float c_gk_node_f[kNodes] = {
+    -0.99800229869339707f, -0.98799251802048538f, -0.96773907567913908f, -0.93727339240070595f,
+    -0.89726453234408188f, -0.84820658341042721f, -0.79041850144246595f, -0.72441773136017007f,
+    -0.65099674129741703f, -0.57097217260853883f, -0.4850818636402397f, -0.39415134707756339f,
+    -0.29918000715316884f, -0.20119409399743451f, -0.10114206691871749f, 0.0f,
+    0.10114206691871749f, 0.20119409399743451f, 0.29918000715316884f, 0.39415134707756339f,
+    0.4850818636402397f, 0.57097217260853883f, 0.65099674129741703f, 0.72441773136017007f,
+    0.79041850144246595f, 0.84820658341042721f, 0.89726453234408188f, 0.93727339240070595f,
+    0.96773907567913908f, 0.98799251802048538f, 0.99800229869339707f};
+__constant__ double c_gk_node_d[kNodes] = {
+    -0.998002298693397060285172840152271209, -0.987992518020485428489565718586612581,
+    -0.967739075679139134257347978784337225, -0.937273392400705904307758947710209471,
+    -0.897264532344081900882509656454495883, -0.848206583410427216200648320774216851,
+    -0.790418501442465932967649294817947347, -0.72441773136017004741618605461393801,
+    -0.650996741297416970533735895313274693, -0.570972172608538847537226737253910641,
+    -0.485081863640239680693655740232350613, -0.394151347077563369897207370981045468,
+    -0.299180007153168812166780024266388963, -0.201194093997434522300628303394596208,
+    -0.101142066918717499027074231447392339, 0.0,
+    0.101142066918717499027074231447392339, 0.201194093997434522300628303394596208,
+    0.299180007153168812166780024266388963, 0.394151347077563369897207370981045468,
+    0.485081863640239680693655740232350613, 0.570972172608538847537226737253910641,
+    0.650996741297416970533735895313274693, 0.72441773136017004741618605461393801,
+    0.790418501442465932967649294817947347, 0.848206583410427216200648320774216851,
+    0.897264532344081900882509656454495883, 0.937273392400705904307758947710209471,
+    0.967739075679139134257347978784337225, 0.987992518020485428489565718586612581,
+    0.998002298693397060285172840152271209};
 
 // ---------------------------------------------------------------------------
 // Small helpers
@@ -175,8 +215,8 @@ __global__ void node_table_kernel(double R, double du, double a, double beta, do
   while (npan < kMaxPanels && panel_table_offset(npan + 1) <= j) ++npan;
   const int64_t off = panel_table_offset(npan);
   int64_t local = j - off;
-  int p = static_cast<int>(local / 15);
-  int k = static_cast<int>(local % 15);
+  int p = static_cast<int>(local / kNodes);
+  int k = static_cast<int>(local % kNodes);
   double hw = R / (2.0 * npan);
   double r = hw * (2.0 * p + 1.0 + gk_node(k));
   double l = r / du;
@@ -316,11 +356,11 @@ __global__ void finish_kernel(const C* __restrict__ grids, const double* __restr
 template <typename T>
 __device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q, int npan, int p0,
                                             int np, double dw, int lane) {
-  const int64_t off = panel_table_offset(npan) + 15 * (int64_t)p0;
+  const int64_t off = panel_table_offset(npan) + kNodes * (int64_t)p0;
   const double* omn = q.node_omn + off;
   const T* hk = static_cast<const T*>(q.node_hk) + off;
   const T* hd = static_cast<const T*>(q.node_hd) + off;
-  for (int j = lane; j < 15 * np; j += 32) {
+  for (int j = lane; j < kNodes * np; j += 32) {
     double t = dw * omn[j];
     t -= rint(t);
     T sn, cs;
@@ -336,146 +376,179 @@ __device__ __forceinline__ void build_nodes(NodeVal<T>* sh, const QuadParams& q,
 }
 
 // FP32 panels are evaluated two nodes at a time in Blackwell's paired FP32
-// arithmetic.  A panel's 15 nodes then sit in kSlots float4 slots:
-//   slot m (m = 0..6)      the node pair (m, 14 - m), i.e. x = -|x_m| (lo) and
-//                          +|x_m| (hi): {w_K h cos lo, hi, w_K h sin lo, hi};
-//   slot 7 + i (i = 0..2)  the Gauss nodes among them (m = 2 i + 1): the same
-//                          with the Gauss weight w_G;
-//   slot 10                the centre node {w_K h cos, w_K h sin, w_G h cos,
-//                          w_G h sin}.
+// arithmetic, on the pairs of neighbouring nodes (2 k, 2 k + 1), k = 0..14,
+// and node 30 alone.  A panel's values sit in kSlots float4 slots:
+//   slot k (0..14)         {w_K h cos, w_K h sin} of the pair as
+//                          {cos 2k, cos 2k+1, sin 2k, sin 2k+1};
+//   slot 15 + k / 2        w_G h {cos, sin} of node 2 k + 1 (every odd node
+//                          is a Gauss node) in components 2 (k & 1) + {0, 1};
+//   slot 23                node 30: {w_K h cos, w_K h sin, 0, 0}.
 // The FP32 node tables hold w_K h and w_G h (zero at Kronrod-only nodes).
-constexpr int kSlots = 11;
+constexpr int kPairs = (kNodes - 1) / 2;   // 15
+constexpr int kSlots = 24;
 static_assert(kSlots * 16 * kPanelBatch <= kNodeBatch * static_cast<int>(sizeof(NodeVal<float>)),
               "packed panels must fit the per-warp node buffer");
 
 __device__ __forceinline__ void build_nodes(NodeVal<float>* sh, const QuadParams& q, int npan,
                                             int p0, int np, double dw, int lane) {
-  const int64_t off = panel_table_offset(npan) + 15 * (int64_t)p0;
+  const int64_t off = panel_table_offset(npan) + kNodes * (int64_t)p0;
   const double* omn = q.node_omn + off;
   const float* hk = static_cast<const float*>(q.node_hk) + off;
   const float* hg = static_cast<const float*>(q.node_hd) + off;
   float* shf = reinterpret_cast<float*>(sh);
-  for (int j = lane; j < 15 * np; j += 32) {
+  for (int j = lane; j < kNodes * np; j += 32) {
     double t = dw * omn[j];
     t -= rint(t);
     float sn, cs;
     sincospif(static_cast<float>(2.0 * t), &sn, &cs);
     const float k = hk[j], g = hg[j];
-    const int p = j / 15, n = j - 15 * p;
+    const int p = j / kNodes, n = j - kNodes * p;
     float* base = shf + 4 * kSlots * p;
-    if (n == 7) {
-      base[40] = k * cs;
-      base[41] = k * sn;
-      base[42] = g * cs;
-      base[43] = g * sn;
+    if (n == kNodes - 1) {
+      base[4 * 23] = k * cs;
+      base[4 * 23 + 1] = k * sn;
+      base[4 * 23 + 2] = 0.f;
+      base[4 * 23 + 3] = 0.f;
     } else {
-      const int hi = n > 7 ? 1 : 0;
-      const int m = hi ? 14 - n : n;
-      base[4 * m + hi] = k * cs;
-      base[4 * m + 2 + hi] = k * sn;
-      if (m & 1) {
-        base[4 * (7 + (m >> 1)) + hi] = g * cs;
-        base[4 * (7 + (m >> 1)) + 2 + hi] = g * sn;
+      const int pr = n >> 1, hi = n & 1;
+      base[4 * pr + hi] = k * cs;
+      base[4 * pr + 2 + hi] = k * sn;
+      if (hi) {
+        base[4 * (15 + (pr >> 1)) + 2 * (pr & 1)] = g * cs;
+        base[4 * (15 + (pr >> 1)) + 2 * (pr & 1) + 1] = g * sn;
       }
     }
   }
 }
 
-// Accumulate panels [0, np) held in sh (global panel index p0 + p) for one
-// tap: Bh = 2 rho h (half-cycles of J0 per unit of the node coordinate).
-// Every node of panel p lies in [a - Bh, a + Bh], a = Bh (2 (p0 + p) + 1);
-// when that whole range is past J0's small-argument formula for every active
-// lane of the warp, the panel runs an unrolled body with the asymptotic
-// formula only (the same values j0_hc gives there), with no per-node branch.
-// FP64 path: the error estimate sums |sum_j (w_K - w_G)_j f_j| per panel.
-template <typename T, bool kLarge>
-__device__ __forceinline__ void panel_nodes(const NodeVal<T>* hp, T Bh, T a, T& kr, T& ki, T& dr,
-                                            T& di) {
-#pragma unroll
-  for (int j = 0; j < 15; ++j) {
-    const T u = fma(Bh, gk_node_c(T(0), j), a);
-    const T J = kLarge ? j0_hc_large(u) : j0_hc(u);
-    const NodeVal<T> v = hp[j];
-    kr = fma(J, v.kr, kr);
-    ki = fma(J, v.ki, ki);
-    dr = fma(J, v.dr, dr);
-    di = fma(J, v.di, di);
-  }
-}
-
+// FP64 path: one rolled loop over the panel's nodes with CUDA's j0, the
+// estimate summing |sum_j (w_K - w_G)_j f_j| per panel.
 template <typename T>
-__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np, T Bh, bool active,
-                                            T& kr, T& ki, T& err) {
+__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np, T Bh, T, T,
+                                            bool, T& kr, T& ki, T& err) {
   for (int p = 0; p < np; ++p) {
     const T a = Bh * static_cast<T>(2 * (p0 + p) + 1);
-    const NodeVal<T>* hp = sh + 15 * p;
+    const NodeVal<T>* hp = sh + kNodes * p;
     T dr = 0, di = 0;
-    if (panel_all_large(a - Bh, active))
-      panel_nodes<T, true>(hp, Bh, a, kr, ki, dr, di);
-    else
-      panel_nodes<T, false>(hp, Bh, a, kr, ki, dr, di);
+#pragma unroll 1
+    for (int j = 0; j < kNodes; ++j) {
+      const T u = fma(Bh, gk_node_c(T(0), j), a);
+      const T J = j0_hc(u);
+      const NodeVal<T> v = hp[j];
+      kr = fma(J, v.kr, kr);
+      ki = fma(J, v.ki, ki);
+      dr = fma(J, v.dr, dr);
+      di = fma(J, v.di, di);
+    }
     err += est_sqrt(dr * dr + di * di);
   }
 }
 
-// One FP32 panel: the seven node pairs in f32x2 arithmetic, the centre node
-// alone.  kMode 2: every node lies past kJ0Far (degree-2 asymptotic form);
-// 1: past J0's split (degree-4 form); 0: the panel straddles the split for
-// some lane, and both the small-argument and the asymptotic form are
-// evaluated and selected per node (no per-node branch).  Returns the panel's
-// Kronrod sum (kr, ki) and Gauss sum (gr, gi).
-template <int kMode>
-__device__ __forceinline__ void panel_pairs(const float4* hp, float Bh, float a, float& kr,
-                                            float& ki, float& gr, float& gi) {
-  float2 KR = make_float2(0.f, 0.f), KI = KR, GR = KR, GI = KR;
+// J0 regime of one node pair, the same for every lane of the warp: the
+// degree-2 asymptotic form when the pair's lower node lies at u >= kJ0Far for
+// every lane, the degree-4 form when it lies past J0's split, the
+// small-argument series when the upper node lies below the split, and both
+// (selected per node) otherwise.
+enum PairRegime { kPairSmall = 0, kPairBoth = 1, kPairNear = 2, kPairFar = 3, kPairFarthest = 4 };
+
+template <int kRegime>
+__device__ __forceinline__ float2 j0_pair_regime(float2 u) {
+  if (kRegime == kPairFarthest) return j0_farthest2(u);
+  if (kRegime == kPairFar) return j0_far2(u);
+  if (kRegime == kPairNear) return j0_large2(u);
+  if (kRegime == kPairSmall) return j0_small2(u);
+  const float2 Js = j0_small2(u), Jl = j0_large2(u);
+  return make_float2(u.x > kJ0Split ? Jl.x : Js.x, u.y > kJ0Split ? Jl.y : Js.y);
+}
+
+// Pair k of one FP32 panel in regime R: J0 at both nodes (x = node
+// coordinates), the Kronrod sums, the Gauss sum of the odd node.
+template <int R>
+__device__ __forceinline__ void panel_pair(float2 x, float4 v, float2 g, float Bh, float a,
+                                           float2& KR, float2& KI, float& gr, float& gi) {
+  const float2 u = make_float2(fmaf(x.x, Bh, a), fmaf(x.y, Bh, a));
+  const float2 J = j0_pair_regime<R>(u);
+  KR = __ffma2_rn(J, make_float2(v.x, v.y), KR);
+  KI = __ffma2_rn(J, make_float2(v.z, v.w), KI);
+  gr = fmaf(J.y, g.x, gr);
+  gi = fmaf(J.y, g.y, gi);
+}
+
+// Pairs [k0, k1) of one FP32 panel in regime R, in a rolled loop (node
+// coordinates from constant memory, values by computed index).
+template <int R>
+__device__ __forceinline__ void panel_pair_range(const float4* hp, int k0, int k1, float Bh,
+                                                 float a, float2& KR, float2& KI, float& gr,
+                                                 float& gi) {
+  const float2* hg = reinterpret_cast<const float2*>(hp + 15);
+#pragma unroll 1
+  for (int k = k0; k < k1; ++k)
+    panel_pair<R>(make_float2(c_gk_node_f[2 * k], c_gk_node_f[2 * k + 1]), hp[k], hg[k], Bh, a,
+                  KR, KI, gr, gi);
+}
+
+// One FP32 panel.  kAllFar = kPairFarthest or kPairFar: every pair is in
+// that regime (degree 1 or 2, unrolled); kAllFar = 0: pair k's regime follows from the warp-uniform counts ks (pairs
+// all below the split), kn (pairs not all past it) and kf (pairs not all
+// past kJ0Far), ks <= kn <= kf: the small-argument series below ks, both
+// formulas below kn, degree 4 up to kf, degree 2 beyond.  Returns the
+// panel's Kronrod sum (kr, ki) and Gauss sum (gr, gi).
+template <int kAllFar>
+__device__ __forceinline__ void panel_sums(const float4* hp, float Bh, float a, int ks, int kn,
+                                           int kf, float& kr, float& ki, float& gr, float& gi) {
+  float2 KR = make_float2(0.f, 0.f), KI = KR;
+  gr = gi = 0.f;
+  if (kAllFar) {
+    const float2* hg = reinterpret_cast<const float2*>(hp + 15);
 #pragma unroll
-  for (int m = 0; m < 7; ++m) {
-    const float x = static_cast<float>(gk_abs_node(m));
-    const float2 u = make_float2(fmaf(-x, Bh, a), fmaf(x, Bh, a));
-    float2 J;
-    if (kMode == 2) {
-      J = j0_far2(u);
-    } else if (kMode == 1) {
-      J = j0_large2(u);
-    } else {
-      const float2 Js = j0_small2(u), Jl = j0_large2(u);
-      J = make_float2(u.x > kJ0Split ? Jl.x : Js.x, u.y > kJ0Split ? Jl.y : Js.y);
-    }
-    const float4 v = hp[m];
-    KR = __ffma2_rn(J, make_float2(v.x, v.y), KR);
-    KI = __ffma2_rn(J, make_float2(v.z, v.w), KI);
-    if (m & 1) {
-      const float4 g = hp[7 + (m >> 1)];
-      GR = __ffma2_rn(J, make_float2(g.x, g.y), GR);
-      GI = __ffma2_rn(J, make_float2(g.z, g.w), GI);
-    }
+    for (int k = 0; k < kPairs; ++k)
+      panel_pair<kAllFar == kPairFarthest ? kPairFarthest : kPairFar>(
+          make_float2(static_cast<float>(gk_node(2 * k)), static_cast<float>(gk_node(2 * k + 1))),
+          hp[k], hg[k], Bh, a, KR, KI, gr, gi);
+  } else {
+    panel_pair_range<kPairSmall>(hp, 0, ks, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairBoth>(hp, ks, kn, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairNear>(hp, kn, kf, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairFar>(hp, kf, kPairs, Bh, a, KR, KI, gr, gi);
   }
-  const float Jc = kMode == 2 ? j0_far(a) : kMode == 1 ? j0_large(a) : j0_halfcycles(a);
-  const float4 c = hp[10];
-  kr = fmaf(Jc, c.x, KR.x + KR.y);
-  ki = fmaf(Jc, c.y, KI.x + KI.y);
-  gr = fmaf(Jc, c.z, GR.x + GR.y);
-  gi = fmaf(Jc, c.w, GI.x + GI.y);
+  // node 30, the panel's last
+  const float u = fmaf(static_cast<float>(gk_node(kNodes - 1)), Bh, a);
+  const float J = kAllFar == kPairFarthest ? j0_farthest(u)
+                  : (kAllFar || kf < kPairs) ? j0_far(u) : j0_halfcycles(u);
+  const float4 c = hp[23];
+  kr = fmaf(J, c.x, KR.x + KR.y);
+  ki = fmaf(J, c.y, KI.x + KI.y);
 }
 
 // FP32: per panel, the Kronrod sum K_p and the Gauss sum G_p; the estimate
 // adds |K_p - G_p|, formed from the panel's own sums (of the panel's size,
-// not the whole integral's).  The panel's formula is chosen by warp votes on
-// its lowest node argument a - Bh.
+// not the whole integral's).  The J0 regime of each node pair follows from
+// the smallest and largest Bh of the warp's active lanes (warp-uniform):
+// node j of panel P lies at u = Bh (2 P + 1 + x_j) for each lane.
 __device__ __forceinline__ void eval_panels(const NodeVal<float>* sh, int p0, int np, float Bh,
-                                            bool active, float& kr, float& ki, float& err) {
+                                            float bh_min, float bh_max, bool active, float& kr,
+                                            float& ki, float& err) {
   const float4* hp = reinterpret_cast<const float4*>(sh);
+  const int lane = threadIdx.x & 31;
   float f = static_cast<float>(2 * p0 + 1);   // 2 (p0 + p) + 1, exact
   for (int p = 0; p < np; ++p, f += 2.f, hp += kSlots) {
     const float a = Bh * f;
-    const float lo = a - Bh;
     float pkr, pki, pgr, pgi;
-    if (__all_sync(0xffffffffu, !active || lo >= kJ0Far))
-      panel_pairs<2>(hp, Bh, a, pkr, pki, pgr, pgi);
-    else if (__all_sync(0xffffffffu, !active || lo > kJ0Split))
-      panel_pairs<1>(hp, Bh, a, pkr, pki, pgr, pgi);
-    else
-      panel_pairs<0>(hp, Bh, a, pkr, pki, pgr, pgi);
+    const float lo_min = bh_min * (f + c_gk_node_f[0]);   // lowest node of any lane
+    if (lo_min >= kJ0Farthest) {
+      panel_sums<kPairFarthest>(hp, Bh, a, 0, 0, 0, pkr, pki, pgr, pgi);
+    } else if (lo_min >= kJ0Far) {
+      panel_sums<kPairFar>(hp, Bh, a, 0, 0, 0, pkr, pki, pgr, pgi);
+    } else {
+      // lane k < 15 classifies pair k; the counts are the same in every lane
+      const bool on = lane < kPairs;
+      const float tlo = f + c_gk_node_f[on ? 2 * lane : 0];
+      const float thi = f + c_gk_node_f[on ? 2 * lane + 1 : 0];
+      const int kf = __popc(__ballot_sync(0xffffffffu, on && !(bh_min * tlo >= kJ0Far)));
+      const int kn = __popc(__ballot_sync(0xffffffffu, on && !(bh_min * tlo > kJ0Split)));
+      const int ks = __popc(__ballot_sync(0xffffffffu, on && bh_max * thi <= kJ0Split));
+      panel_sums<0>(hp, Bh, a, ks, kn, kf, pkr, pki, pgr, pgi);
+    }
     kr += pkr;
     ki += pki;
     const float dr = pkr - pgr, di = pki - pgi;
@@ -497,15 +570,23 @@ __device__ __forceinline__ double panel_bh(const QuadParams& q, double rho, int 
 // while any active tap misses the tolerance, up to max_panels (the node
 // tables' largest partition) and max_refine doublings.  `built` (the panel
 // count whose nodes are resident in sh, or 0) is warp-uniform and updated.
-template <typename T, typename C>
-__device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active, double dw,
-                        int npan, int max_panels, int& built, bool& ok, int lane,
-                        unsigned long long& nodes) {
+template <typename T, typename C, typename N>
+__device__ __forceinline__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
+                                        double dw, int npan, int max_panels, int& built, bool& ok,
+                                        int lane, N& nodes) {
   npan = min(npan, max_panels);
+  // the active lanes' extreme radii (warp-uniform)
+  T rmin = active ? rho : T(1e30), rmax = active ? rho : T(0);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
   int refine = 0;
   while (true) {
-    nodes += active ? 15ull * npan : 0ull;
+    nodes += active ? static_cast<N>(kNodes * npan) : N(0);
     const T Bh = panel_bh(q, rho, npan);
+    const T bmin = panel_bh(q, rmin, npan), bmax = panel_bh(q, rmax, npan);
     T kr = 0, ki = 0, err = 0;
     if (npan <= kPanelBatch) {
       if (built != npan) {
@@ -514,14 +595,14 @@ __device__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
         __syncwarp();
         built = npan;
       }
-      eval_panels(sh, 0, npan, Bh, active, kr, ki, err);
+      eval_panels(sh, 0, npan, Bh, bmin, bmax, active, kr, ki, err);
     } else {
       for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
         const int nb = min(kPanelBatch, npan - p0);
         __syncwarp();
         build_nodes(sh, q, npan, p0, nb, dw, lane);
         __syncwarp();
-        eval_panels(sh, p0, nb, Bh, active, kr, ki, err);
+        eval_panels(sh, p0, nb, Bh, bmin, bmax, active, kr, ki, err);
       }
       built = 0;
     }
@@ -768,10 +849,8 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
     const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
     const int half = Jw / 2;
     const T fu = r.fu, fv = r.fv;
-    const T aw = static_cast<T>(fabs(r.dw)) * tv.inv_hw;
-    // the comparison also sends a NaN to the last row instead of an
-    // undefined conversion
-    const int jrow = aw < static_cast<T>(nw - 2) ? static_cast<int>(aw) : nw - 2;
+    const T aw = table_w_scaled(static_cast<T>(fabs(r.dw)), tv.inv_hw);
+    const int jrow = table_w_row(aw, nw - 2);
     const T fw = aw - static_cast<T>(jrow);
     const bool neg = r.dw < 0.0;
     const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
@@ -876,8 +955,8 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
       const VisRec<T> r = recs[ri];
       const int Jw = r.jw;
       const int half = Jw / 2;
-      const T aw = static_cast<T>(fabs(r.dw)) * tv.inv_hw;
-      const int jrow = aw < static_cast<T>(nw - 2) ? static_cast<int>(aw) : nw - 2;
+      const T aw = table_w_scaled(static_cast<T>(fabs(r.dw)), tv.inv_hw);
+      const int jrow = table_w_row(aw, nw - 2);
       const T fw = aw - static_cast<T>(jrow);
       const bool neg = r.dw < 0.0;
       const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
@@ -943,6 +1022,101 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
       }
       __syncthreads();
     }
+  }
+  flush_counts(stats, 0, my_taps, 0, lane);
+}
+
+// Degrid / grid with the tabulated kernel, one thread block per w-row work
+// item (grid_staging 2): the block copies the item's pair of adjacent
+// w-planes, all n_rho radii, into shared memory once, then its warps take the
+// item's visibilities (every kept visibility whose |dw| falls on that row)
+// one at a time and read both entries of every tap from shared memory.  A
+// tap's 16-byte table entries are scattered over the row, one cache line
+// each from global memory; from shared memory they cost a bank access.  The
+// taps, their order and arithmetic are those of vis_table_kernel.
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256) row_table_kernel(
+    const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm,
+    const uint32_t* __restrict__ row_idx, const int32_t* __restrict__ item_se,
+    const uint32_t* __restrict__ item_key, int n_items, const C* __restrict__ grid_in,
+    C* grid_out, const C* __restrict__ vis_in, C* __restrict__ vis_out, TableView<T> tv,
+    int npad, const int32_t* __restrict__ stack_slot, unsigned long long* head,
+    unsigned long long* stats) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  KPair<C>* row = reinterpret_cast<KPair<C>*>(smem_raw);
+  __shared__ int s_item;
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
+  const int nr = static_cast<int>(tv.nr);
+  const T last_r = static_cast<T>(nr - 2);
+  unsigned long long my_taps = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(head, 1ULL));
+    __syncthreads();
+    const int item = s_item;
+    if (item >= n_items) break;
+    const int jrow = static_cast<int>(item_key[item] & 0xffffffu);
+    const KPair<C>* src = pairs + static_cast<int64_t>(jrow) * nr;
+    for (int c = threadIdx.x; c < nr; c += blockDim.x) row[c] = src[c];
+    __syncthreads();
+    const int r0 = item_se[2 * item], r1 = item_se[2 * item + 1];
+    for (int ri = r0 + warp; ri < r1; ri += nwarps) {
+      const uint32_t rec = row_idx[ri];
+      const VisRec<T> r = recs[rec];
+      const int Jw = r.jw;
+      const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
+      const int half = Jw / 2;
+      const T fu = r.fu, fv = r.fv;
+      // the item's row is this record's (the plan keyed it with the same
+      // arithmetic), so fw lies in [0, 1]
+      const T fw = table_w_scaled(static_cast<T>(fabs(r.dw)), tv.inv_hw) - static_cast<T>(jrow);
+      const bool neg = r.dw < 0.0;
+      const uint32_t pm = perm[rec];
+      const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                         : cmake<C>(0.0, 0.0);
+      C accv = cmake<C>(0.0, 0.0);
+      const int ntap = Jw * Jw;
+      int a = lane % Jw, b = lane / Jw;
+      const int step_b = 32 / Jw, step_a = 32 % Jw;
+      T du_ = fu - static_cast<T>(a - half + 1), dv_ = fv - static_cast<T>(b - half + 1);
+      const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
+      const T fJw = static_cast<T>(Jw);
+      #pragma unroll 4
+      for (int t0 = 0; t0 < ntap; t0 += 32) {
+        if (t0 + lane < ntap) {
+          const int ou = a - half + 1, ov = b - half + 1;
+          const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
+          int ir;
+          T fr;
+          table_index(sr, nr - 2, last_r, ir, fr);
+          const KPair<C> p0 = row[ir], p1 = row[ir + 1];
+          const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
+          const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
+          C K;
+          K.x = fma(fw, hi_x - lo_x, lo_x);
+          K.y = fma(fw, hi_y - lo_y, lo_y);
+          if (neg) K.y = -K.y;
+          ++my_taps;
+          const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                             wrap_index(r.bu + ou, npad);
+          apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
+        }
+        a += step_a;
+        b += step_b;
+        du_ -= fstep_a;
+        dv_ -= fstep_b;
+        if (a >= Jw) {
+          a -= Jw;
+          ++b;
+          du_ += fJw;
+          dv_ -= T(1);
+        }
+      }
+      if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
+    }
+    __syncthreads();   // the row is rewritten by the next item
   }
   flush_counts(stats, 0, my_taps, 0, lane);
 }
@@ -1417,6 +1591,42 @@ int launch_tile_table(Plan& p, int k, const C* grids_in, C* grids_out, const C* 
   return PHI_OK;
 }
 
+// One launch over the w-row work items of the group's stacks (grid_staging
+// 2).  Sets `launched` to false (and launches nothing) when one row of the
+// table does not fit a thread block's shared memory; the caller then runs
+// the unstaged kernel.
+template <typename T, typename C, bool kGrid>
+int launch_row_table(Plan& p, int g, const C* grids_in, C* grids_out, const C* vis_in,
+                     C* vis_out, cudaStream_t s, bool& launched) {
+  launched = false;
+  const int64_t s0 = p.group_off[g], s1 = p.group_off[g + 1];
+  const int64_t i0 = p.stack_item_off[p.group_stacks[s0]];
+  const int64_t ni = p.stack_item_off[p.group_stacks[s1 - 1] + 1] - i0;
+  const size_t smem = sizeof(KPair<C>) * static_cast<size_t>(p.table_nr);
+  int dev = 0, optin = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (smem > static_cast<size_t>(optin)) return PHI_OK;
+  launched = true;
+  if (ni == 0) return PHI_OK;
+  PHI_CUDA_TRY(cudaFuncSetAttribute(row_table_kernel<T, C, kGrid>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(smem)));
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_table_kernel<T, C, kGrid>,
+                                                    kVisThreads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t want = static_cast<int64_t>(per_sm) * p.num_sms;
+  const int blocks = static_cast<int>(ni < want ? ni : want);
+  row_table_kernel<T, C, kGrid><<<blocks, kVisThreads, smem, s>>>(
+      static_cast<const VisRec<T>*>(p.recs), p.perm, p.row_idx, p.item_start + 2 * i0,
+      p.item_key + i0, static_cast<int>(ni), grids_in, grids_out, vis_in, vis_out,
+      table_view<T, C>(p), p.npad, p.stack_slot_dev, p.counters + g, p.counters + p.K);
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
 // In-place FFTs of the first n grids of the group (one batched call when
 // the group is full).
 template <typename T, typename C>
@@ -1509,7 +1719,13 @@ int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C
     return launch_dde<T, C, kGrid>(p, static_cast<const VisRec<T>*>(p.recs) + b0, b0, nk, g,
                                    grids_in, grids_out, vis_in, vis_out, *dde, s);
   }
-  if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.d.grid_staging) {
+  if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.d.grid_staging == 2) {
+    bool launched = false;
+    PHI_TRY_ST((launch_row_table<T, C, kGrid>(p, g, grids_in, grids_out, vis_in, vis_out, s,
+                                              launched)));
+    if (launched) return PHI_OK;
+  }
+  if (p.d.kernel_mode == PHI_KERNEL_TABLE && p.d.grid_staging == 1) {
     for (int64_t i = s0; i < s1; ++i)
       PHI_TRY_ST((launch_tile_table<T, C, kGrid>(p, p.group_stacks[i], grids_in, grids_out, vis_in,
                                                  vis_out, s)));
@@ -1823,7 +2039,8 @@ namespace phi {
 namespace {
 
 constexpr int kNoAllocMaxPanels = PHI_WKERNEL_NOALLOC_MAX_PANELS;
-constexpr int64_t kNoAllocNodes = 15LL * kNoAllocMaxPanels * (kNoAllocMaxPanels + 1) / 2;
+constexpr int64_t kNoAllocNodes =
+    static_cast<int64_t>(kNodes) * kNoAllocMaxPanels * (kNoAllocMaxPanels + 1) / 2;
 constexpr size_t kNoAllocBytes = PHI_WKERNEL_NOALLOC_SCRATCH_BYTES;
 static_assert(kNoAllocBytes == 256 + 3 * 8 * kNoAllocNodes, "scratch layout");
 

@@ -15,6 +15,7 @@
 #include <new>
 
 #include "phi_internal.cuh"
+#include "table_index.cuh"
 
 namespace phi {
 
@@ -252,6 +253,21 @@ __global__ void tile_scatter_kernel(const uint32_t* __restrict__ keys,
     }
 }
 
+// Table path, w-row staging: per kept record (sorted order) the key
+// (stack, w-row of its |dw|), the row computed in precision T exactly as the
+// table kernels compute it, and the record's index.
+template <typename T>
+__global__ void row_key_kernel(const VisRec<T>* __restrict__ recs, int64_t n, T inv_hw,
+                               int last_row, uint32_t* __restrict__ keys,
+                               uint32_t* __restrict__ vals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int row = table_w_row(table_w_scaled(static_cast<T>(fabs(recs[i].dw)), inv_hw), last_row);
+    keys[i] = (static_cast<uint32_t>(recs[i].stack) << 24) | static_cast<uint32_t>(row);
+    vals[i] = static_cast<uint32_t>(i);
+  }
+}
+
 struct Scratch {
   std::vector<void*> ptrs;
   ~Scratch() {
@@ -288,6 +304,7 @@ void free_plan(Plan* p) {
   cudaFree(p->table);
   cudaFree(p->item_start);
   cudaFree(p->item_key);
+  cudaFree(p->row_idx);
   cudaFree(p->group_stacks_dev);
   cudaFree(p->stack_slot_dev);
   cudaFree(p->wbar_dev);
@@ -333,7 +350,7 @@ int validate(const phi_plan_desc& d, int64_t M) {
   if (d.kernel_mode != PHI_KERNEL_QUADRATURE && d.kernel_mode != PHI_KERNEL_TABLE &&
       d.kernel_mode != PHI_KERNEL_RADIAL)
     return PHI_ERR_ARG;
-  if (d.grid_staging != 0 && d.grid_staging != 1) return PHI_ERR_ARG;
+  if (d.grid_staging < 0 || d.grid_staging > 2) return PHI_ERR_ARG;
   if (d.max_grid_mib < 0 || d.reserved0 != 0) return PHI_ERR_ARG;
   if (d.grid_staging && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
   if (d.kernel_mode == PHI_KERNEL_TABLE && !(d.table_tol > 0.0 && d.table_tol < 1.0))
@@ -398,9 +415,12 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   p.n_win = std::sqrt(1.0 - p.l_win * p.l_win);
   p.c_support = p.l_win / (p.n_win * p.du);
   const double tol = std::min(d.quad_rel_tol, d.quad_abs_tol);
+  // Gauss-Kronrod 15/31 panels of about 6 integrand cycles at the paper's
+  // tolerance 1e-6, narrowing slowly with the tolerance (3.4 cycles at 1e-12):
+  // the widths that gave the fewest tap-nodes, refinements included
   p.cycles_per_panel = d.cycles_per_panel > 0.0
                            ? d.cycles_per_panel
-                           : std::min(2.5, std::max(0.25, 1.75 * std::pow(tol / 1e-6, 1.0 / 11.0)));
+                           : std::min(8.0, std::max(1.0, 6.0 * std::pow(tol / 1e-6, 1.0 / 24.0)));
 
   int dev = 0;
   PHI_CUDA_TRY(cudaGetDevice(&dev));
@@ -563,21 +583,66 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
     PHI_CUDA_TRY(cudaGetLastError());
   }
 
-  // --- uv-tile work items for the table path: tiles of the sorted kept
-  // records, split into items of at most kItemRecords records
+  // --- table geometry (Sec. 5.1.1): sample spacing from the bilinear error
+  // bound (half the budget per direction): h^2/8 times the second
+  // derivative, bounded by (2 pi R)^2 in rho and (2 pi (1 - n_win))^2 in w
+  if (d.kernel_mode == PHI_KERNEL_TABLE) {
+    p.table_hr = std::sqrt(4.0 * d.table_tol) / (2.0 * kPi * p.R);
+    p.table_hw = std::sqrt(4.0 * d.table_tol) / (2.0 * kPi * (1.0 - p.n_win));
+    double dmax = 0.0;
+    for (int q = 0; q < K; ++q) dmax = std::max(dmax, p.stack_maxabs[q]);
+    const double rmax = std::sqrt(2.0) * std::max(p.max_jw, d.support) / 2.0 + 2.0;
+    p.table_nr = static_cast<int64_t>(std::ceil(rmax / p.table_hr)) + 2;
+    p.table_nw = static_cast<int64_t>(std::ceil(dmax / p.table_hw)) + 2;
+    if (p.table_nr * p.table_nw > (int64_t(1) << 31) || p.table_nw - 2 >= (1 << 24))
+      return PHI_ERR_ARG;
+  }
+
+  // --- work items of the table path's staged kernels: runs of equal key in
+  // the sorted kept records (grid_staging 1: uv tiles, in record order;
+  // grid_staging 2: w-rows, through the index p.row_idx), split into items of
+  // at most max_records records
   p.tile = tile;
   p.tiles_per_row = tiles_per_row;
   p.stack_item_off.assign(K + 1, 0);
   p.stack_staged.assign(K, 0);
   if (d.kernel_mode == PHI_KERNEL_TABLE && d.grid_staging && p.n_kept > 0) {
     const int64_t n = p.n_kept;
+    const uint32_t* ikeys = skeys;   // uv-tile keys of the kept records, in order
+    int max_records = kItemRecords;
+    if (d.grid_staging == 2) {
+      uint32_t *rk = nullptr, *rv = nullptr, *rks = nullptr;
+      PHI_CUDA_TRY(tmp.alloc(&rk, n));
+      PHI_CUDA_TRY(tmp.alloc(&rv, n));
+      PHI_CUDA_TRY(tmp.alloc(&rks, n));
+      PHI_CUDA_TRY(owned_alloc(p, &p.row_idx, n));
+      const int last_row = static_cast<int>(p.table_nw - 2);
+      if (f64)
+        row_key_kernel<double><<<nblk, kPlanThreads, 0, s>>>(
+            static_cast<const VisRec<double>*>(p.recs), n, 1.0 / p.table_hw, last_row, rk, rv);
+      else
+        row_key_kernel<float><<<nblk, kPlanThreads, 0, s>>>(
+            static_cast<const VisRec<float>*>(p.recs), n, static_cast<float>(1.0 / p.table_hw),
+            last_row, rk, rv);
+      PHI_CUDA_TRY(cudaGetLastError());
+      size_t bytes = 0;
+      cub::DeviceRadixSort::SortPairs(nullptr, bytes, rk, rks, rv, p.row_idx,
+                                      static_cast<int>(n), 0, 32, s);
+      void* sort_tmp = nullptr;
+      PHI_CUDA_TRY(tmp.alloc(reinterpret_cast<unsigned char**>(&sort_tmp), bytes));
+      if (cub::DeviceRadixSort::SortPairs(sort_tmp, bytes, rk, rks, rv, p.row_idx,
+                                          static_cast<int>(n), 0, 32, s) != cudaSuccess)
+        return PHI_ERR_CUDA;
+      ikeys = rks;
+      max_records = kRowItemRecords;
+    }
     uint32_t *flag = nullptr, *pos = nullptr, *tkey = nullptr;
     int32_t* tstart = nullptr;
     PHI_CUDA_TRY(tmp.alloc(&flag, n));
     PHI_CUDA_TRY(tmp.alloc(&pos, n));
     PHI_CUDA_TRY(tmp.alloc(&tkey, n));
     PHI_CUDA_TRY(tmp.alloc(&tstart, n));
-    tile_flag_kernel<<<nblk, kPlanThreads, 0, s>>>(skeys, n, flag);
+    tile_flag_kernel<<<nblk, kPlanThreads, 0, s>>>(ikeys, n, flag);
     PHI_CUDA_TRY(cudaGetLastError());
     size_t scan_bytes = 0;
     cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, flag, pos, static_cast<int>(n), s);
@@ -586,47 +651,33 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
     if (cub::DeviceScan::ExclusiveSum(scan_tmp, scan_bytes, flag, pos, static_cast<int>(n), s) !=
         cudaSuccess)
       return PHI_ERR_CUDA;
-    tile_scatter_kernel<<<nblk, kPlanThreads, 0, s>>>(skeys, flag, pos, n, tstart, tkey);
+    tile_scatter_kernel<<<nblk, kPlanThreads, 0, s>>>(ikeys, flag, pos, n, tstart, tkey);
     PHI_CUDA_TRY(cudaGetLastError());
     uint32_t last[2] = {0, 0};
     PHI_CUDA_TRY(cudaMemcpyAsync(&last[0], pos + n - 1, 4, cudaMemcpyDeviceToHost, s));
     PHI_CUDA_TRY(cudaMemcpyAsync(&last[1], flag + n - 1, 4, cudaMemcpyDeviceToHost, s));
     PHI_CUDA_TRY(cudaStreamSynchronize(s));
-    const int64_t n_tiles = static_cast<int64_t>(last[0]) + last[1];
-    std::vector<int32_t> hstart(n_tiles + 1);
-    std::vector<uint32_t> hkey(n_tiles);
-    PHI_CUDA_TRY(cudaMemcpyAsync(hstart.data(), tstart, 4 * n_tiles, cudaMemcpyDeviceToHost, s));
-    PHI_CUDA_TRY(cudaMemcpyAsync(hkey.data(), tkey, 4 * n_tiles, cudaMemcpyDeviceToHost, s));
+    const int64_t n_runs = static_cast<int64_t>(last[0]) + last[1];
+    std::vector<int32_t> hstart(n_runs + 1);
+    std::vector<uint32_t> hkey(n_runs);
+    PHI_CUDA_TRY(cudaMemcpyAsync(hstart.data(), tstart, 4 * n_runs, cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaMemcpyAsync(hkey.data(), tkey, 4 * n_runs, cudaMemcpyDeviceToHost, s));
     PHI_CUDA_TRY(cudaStreamSynchronize(s));
-    hstart[n_tiles] = static_cast<int32_t>(n);
-    std::vector<int32_t> istart;
+    hstart[n_runs] = static_cast<int32_t>(n);
+    // items: start and end interleaved, item_start[2 i] = start, [2 i + 1] = end
+    std::vector<int32_t> se;
     std::vector<uint32_t> ikey;
     int cur_stack = -1;
-    for (int64_t t = 0; t < n_tiles; ++t) {
+    for (int64_t t = 0; t < n_runs; ++t) {
       const int st = static_cast<int>(hkey[t] >> 24);
       while (cur_stack < st) p.stack_item_off[++cur_stack] = static_cast<int64_t>(ikey.size());
-      for (int32_t r = hstart[t]; r < hstart[t + 1]; r += kItemRecords) {
-        istart.push_back(r);
+      for (int32_t r = hstart[t]; r < hstart[t + 1]; r += max_records) {
+        se.push_back(r);
+        se.push_back(std::min<int32_t>(r + max_records, hstart[t + 1]));
         ikey.push_back(hkey[t]);
       }
     }
     while (cur_stack < K) p.stack_item_off[++cur_stack] = static_cast<int64_t>(ikey.size());
-    istart.push_back(static_cast<int32_t>(n));
-    // item i ends where item i + 1 starts, or at its tile's end for the last
-    // item of a tile: record the ends via the next start, fixing tile ends
-    std::vector<int32_t> iend(ikey.size());
-    {
-      size_t i = 0;
-      for (int64_t t = 0; t < n_tiles; ++t)
-        for (int32_t r = hstart[t]; r < hstart[t + 1]; r += kItemRecords, ++i)
-          iend[i] = std::min<int32_t>(r + kItemRecords, hstart[t + 1]);
-    }
-    // store start and end interleaved: item_start[2 i] = start, [2 i + 1] = end
-    std::vector<int32_t> se(2 * ikey.size());
-    for (size_t i = 0; i < ikey.size(); ++i) {
-      se[2 * i] = istart[i];
-      se[2 * i + 1] = iend[i];
-    }
     for (int q = 0; q < K; ++q) p.stack_staged[q] = 1;
     PHI_CUDA_TRY(owned_alloc(p, &p.item_start, se.size()));
     PHI_CUDA_TRY(owned_alloc(p, &p.item_key, ikey.size()));
@@ -674,17 +725,6 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   PHI_TRY(launch_node_tables(p, s));
   PHI_TRY(launch_pixel_tables(p, s));
   if (d.kernel_mode == PHI_KERNEL_TABLE) {
-    // Sample spacing from the bilinear error bound (half the budget per
-    // direction): h^2/8 times the second derivative, bounded by (2 pi R)^2 in
-    // rho and (2 pi (1 - n_win))^2 in w.
-    p.table_hr = std::sqrt(4.0 * d.table_tol) / (2.0 * kPi * p.R);
-    p.table_hw = std::sqrt(4.0 * d.table_tol) / (2.0 * kPi * (1.0 - p.n_win));
-    double dmax = 0.0;
-    for (int q = 0; q < K; ++q) dmax = std::max(dmax, p.stack_maxabs[q]);
-    const double rmax = std::sqrt(2.0) * std::max(p.max_jw, d.support) / 2.0 + 2.0;
-    p.table_nr = static_cast<int64_t>(std::ceil(rmax / p.table_hr)) + 2;
-    p.table_nw = static_cast<int64_t>(std::ceil(dmax / p.table_hw)) + 2;
-    if (p.table_nr * p.table_nw > (int64_t(1) << 31)) return PHI_ERR_ARG;
     const size_t pair = 2 * 2 * tsize;
     PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.table),
                              pair * (p.table_nw - 1) * p.table_nr));

@@ -48,4 +48,29 @@ PHI_HD inline void table_index(double s, int last, double last_f, int& ir, doubl
   fr = s - static_cast<double>(ir);
 }
 
+// w-row of a visibility: a = |dw| / h_w as one correctly rounded product (no
+// contraction into a later subtraction), its row j = floor(a) clamped to the
+// last pair of planes, and the fraction fw = a - j.  Every table kernel and
+// the plan's w-row key use this one definition, so they agree bit for bit.
+PHI_HD inline float table_w_scaled(float adw, float inv_hw) {
+#if defined(__CUDA_ARCH__)
+  return __fmul_rn(adw, inv_hw);
+#else
+  return adw * inv_hw;
+#endif
+}
+PHI_HD inline double table_w_scaled(double adw, double inv_hw) {
+#if defined(__CUDA_ARCH__)
+  return __dmul_rn(adw, inv_hw);
+#else
+  return adw * inv_hw;
+#endif
+}
+template <typename T>
+PHI_HD inline int table_w_row(T aw, int last) {
+  // the comparison also sends a NaN to the last row instead of an undefined
+  // conversion
+  return aw < static_cast<T>(last) ? static_cast<int>(aw) : last;
+}
+
 }  // namespace phi

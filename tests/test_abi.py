@@ -144,3 +144,11 @@ def test_no_device_is_an_error_not_a_fallback():
     assert st == phi.PHI_ERR_CUDA
     with pytest.raises(Exception):
         phi.Plan(torch.zeros(4, 3, dtype=torch.float64), image_n=128, fov_rad=0.35)
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's copies of the header's #define limits."""
+    import re
+    text = open(os.path.join(ROOT, "include", "phi.h")).read()
+    m = re.search(r"#define PHI_WKERNEL_NOALLOC_MAX_PANELS (\d+)", text)
+    assert m and int(m.group(1)) == phi.WKERNEL_NOALLOC_MAX_PANELS

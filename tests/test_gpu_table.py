@@ -47,7 +47,7 @@ def test_table_geometry_matches_oracle(case, precision):
     assert abs(info["table_h_rho"] - tab.hr) < 1e-15 and abs(info["table_h_w"] - tab.hw) < 1e-15
 
 
-@pytest.mark.parametrize("staging", [0, 1])
+@pytest.mark.parametrize("staging", [0, 1, 2])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
 def test_table_degrid_and_grid_match_oracle(case, precision, staging):
     plan = plan_for(case, precision, staging)
@@ -116,10 +116,13 @@ def test_table_close_to_quadrature_at_full_size():
                   conj_fold=int(wl.conj_fold))
     x = torch.from_numpy(W.point_sources(wl.image_n, wl.n_sources, wl.seed)).cuda().float()
     ys = {}
-    for mode in ("quadrature", "table"):
-        p = phi.Plan(uvw, kernel_mode=mode, table_tol=1e-4, **common)
-        ys[mode] = p.degrid(x).to(torch.complex128)
+    for mode, staging in (("quadrature", 0), ("table", 0), ("table", 2)):
+        p = phi.Plan(uvw, kernel_mode=mode, table_tol=1e-4, grid_staging=staging, **common)
+        ys[(mode, staging)] = p.degrid(x).to(torch.complex128)
         p.close()
+    # the w-row-staged kernel: the same taps, order and arithmetic
+    assert torch.equal(ys[("table", 2)], ys[("table", 0)])
+    ys = {"table": ys[("table", 0)], "quadrature": ys[("quadrature", 0)]}
     d = ys["table"] - ys["quadrature"]
     scale = torch.abs(ys["quadrature"]).max()
     assert (torch.linalg.vector_norm(d) / torch.linalg.vector_norm(ys["quadrature"])).item() < 1e-4
@@ -152,3 +155,21 @@ def test_table_at_maximum_support_matches_oracle():
     assert O.rel_l2(y, O.degrid_table(op, x, tab)) < 1e-5
     xg = plan.grid(torch.from_numpy(yr).cuda().to(torch.complex64)).cpu().numpy()
     assert O.rel_l2(xg, O.grid_table(op, yr, tab)) < 1e-5
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_row_staging_equals_the_unstaged_kernel(case, precision):
+    """grid_staging 2 (one w-row of the table staged in shared memory for all
+    visibilities on it) evaluates the same taps in the same order and
+    arithmetic as the unstaged kernel: degrid is bitwise equal; grid differs
+    only by the order of the FP atomics."""
+    p0, p2 = plan_for(case, precision, 0), plan_for(case, precision, 2)
+    rd = torch.float64 if precision == "f64" else torch.float32
+    cd = torch.complex128 if precision == "f64" else torch.complex64
+    x = torch.from_numpy(case["x"]).to("cuda", rd)
+    assert torch.equal(p0.degrid(x), p2.degrid(x))
+    y = torch.from_numpy(case["yr"]).to("cuda", cd)
+    g0, g2 = p0.grid(y), p2.grid(y)
+    assert (torch.linalg.vector_norm(g2 - g0) / torch.linalg.vector_norm(g0)).item() < (
+        1e-12 if precision == "f64" else 1e-6)
+    assert p2.stats()[1] == p0.stats()[1]

@@ -75,3 +75,14 @@ def test_j0_far_against_scipy():
     # and it agrees with the degree-4 form to the two fits' errors plus rounding
     near = host_j0(u, "j0_large").astype(np.float64)
     assert np.max(np.abs(near - got)) < 2e-7 + 4 * np.max(env * np.pi * ulp)
+
+
+def test_j0_farthest_against_scipy():
+    """The degree-1 form used for panels whose nodes all lie at u >= 4.5."""
+    u = np.concatenate([np.linspace(4.5, 12.0, 40001), np.linspace(12.0, 130.0, 60001)]
+                       ).astype(np.float32)
+    got = host_j0(u, "j0_farthest").astype(np.float64)
+    ref = sp.j0(np.pi * u.astype(np.float64))
+    env = np.sqrt(2.0 / (np.pi * np.pi * u))
+    ulp = np.spacing(u).astype(np.float64)
+    assert np.all(np.abs(got - ref) <= 2e-7 + 2 * env * np.pi * ulp)

@@ -26,7 +26,7 @@ pytestmark = pytest.mark.gpu
 
 def _plan_and_params(precision):
     tol = 1e-12 if precision == "f64" else 1e-6
-    cpp = 0.5 if precision == "f64" else 1.75
+    cpp = 3.4 if precision == "f64" else 6.0   # the plans' default widths at these tolerances
     uvw = W.uvw_disk(16, 60.0, 40.0, 0)
     plan = phi.Plan(torch.from_numpy(uvw), image_n=128, fov_rad=math.radians(20.0),
                     n_stacks=1, precision=precision, quad_rel_tol=tol, quad_abs_tol=tol,
