@@ -256,7 +256,7 @@ def profiled_fp64():
     """DP flops per tap-node and FP64-pipe activity of vis_kernel<double> from
     the committed small-case ncu capture, or None when the kernel sources
     changed since it was taken."""
-    p = os.path.join(ROOT, "profiles", "vis_kernel_f64_degrid_mwa-2048-first20000.md")
+    p = os.path.join(ROOT, "profiles", "vis_kernel_f64_degrid_mwa-2048-first2000.md")
     if not os.path.exists(p):
         return None
     vals = {}
@@ -268,7 +268,7 @@ def profiled_fp64():
         return None
     keys = ("fp64_flops_per_tap_node", "fp64_pipe_pct", "issue_active_pct")
     out = {k: float(vals[k]) for k in keys if k in vals}
-    out["source"] = "profiles/vis_kernel_f64_degrid_mwa-2048-first20000.md"
+    out["source"] = "profiles/vis_kernel_f64_degrid_mwa-2048-first2000.md"
     return out
 
 

@@ -223,7 +223,9 @@ class Server:
                             started = True
                             break
                 if not started:
-                    self._lock.wait(timeout=0.05)
+                    # nothing fits now: every change that can make room (a
+                    # request finishing, a new one arriving, close) notifies
+                    self._lock.wait()
 
     # ---------------------------------------------------------------- worker
     def _work(self, req, fut, arrival, need, sid, admitted):
