@@ -1087,7 +1087,7 @@ def run_dde(args):
     plan = phi.Plan(torch.from_numpy(uvw_np).to(dev), image_n=wl.image_n,
                     fov_rad=math.radians(wl.fov_deg), n_stacks=16, conj_fold=0)
     info = plan.info()
-    x = torch.from_numpy(x_np).to(dev, rdt)
+    x = torch.from_numpy(x_np).to(dev, torch.float32)
     y = torch.from_numpy(W.random_vis(len(uvw_np), 4)).to(dev, torch.complex64)
     a = torch.from_numpy(a_np).to(dev, torch.complex64)
     b = torch.from_numpy(b_np).to(dev, torch.complex64)
