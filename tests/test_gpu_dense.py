@@ -8,7 +8,7 @@ of oracle time, too long for a test).  For every stack it holds the busiest
 grid cell of the full workload (960 to 2,552 contributions) and every kept
 visibility whose tap box covers it; gridding those visibilities accumulates
 that cell exactly as the full run does (Eq. stacked adjoint), in the FP32
-atomics of the timed kernel.  Gate: relative L2 <= 1e-5 (the benchmark spec), on the
+atomics of the timed kernel.  Gate: relative L2 <= 1e-5 (the FP32 path's), on the
 sub-observation built with the full plan's centres and supports, and on the
 full plan in the bench's launch configuration.
 """
