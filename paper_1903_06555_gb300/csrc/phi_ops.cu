@@ -173,14 +173,23 @@ __device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
   atomicAdd(&p->y, v.y);
 }
 
-// Circular grid index q mod n in 32-bit arithmetic; the division only runs
-// for taps that actually cross the grid edge.  (64-bit integer division and
-// conversions execute on the FP64 unit, about 1/64 of the FP32 rate here.)
+// Circular grid index q mod n outside the loops: a division by a run-time n
+// (its int <-> float conversions run on the FP64 unit, about 1/64 of the FP32
+// rate here).  Not inlined, so that its call can be skipped by a branch
+// rather than if-converted into every tap.
+__device__ __noinline__ int wrap_index_mod(int q, int n) {
+  q %= n;
+  return q < 0 ? q + n : q;
+}
+
+// Circular grid index q mod n in 32-bit arithmetic.  The records hold
+// centred cell indices (the box of a kept visibility lies within
+// [-n/2 - J_w/2, n/2 + J_w/2]), so one conditional add or subtract of n
+// wraps every tap; anything farther out takes the division.
 __device__ __forceinline__ int wrap_index(int q, int n) {
-  if (static_cast<unsigned>(q) >= static_cast<unsigned>(n)) {
-    q %= n;
-    if (q < 0) q += n;
-  }
+  if (q < 0) q += n;
+  if (q >= n) q -= n;
+  if (static_cast<unsigned>(q) >= static_cast<unsigned>(n)) q = wrap_index_mod(q, n);
   return q;
 }
 
@@ -421,26 +430,36 @@ __device__ __forceinline__ void build_nodes(NodeVal<float>* sh, const QuadParams
   }
 }
 
-// FP64 path: one rolled loop over the panel's nodes with CUDA's j0, the
-// estimate summing |sum_j (w_K - w_G)_j f_j| per panel.
-template <typename T>
-__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np, T Bh, T, T,
-                                            bool, T& kr, T& ki, T& err) {
+// FP64 path: one rolled loop over the panel's nodes with CUDA's j0 for each
+// of the lane's NT taps, the estimate summing |sum_j (w_K - w_G)_j f_j| per
+// panel.
+template <typename T, int NT>
+__device__ __forceinline__ void eval_panels(const NodeVal<T>* sh, int p0, int np,
+                                            const T (&Bh)[NT], T (&kr)[NT], T (&ki)[NT],
+                                            T (&err)[NT]) {
   for (int p = 0; p < np; ++p) {
-    const T a = Bh * static_cast<T>(2 * (p0 + p) + 1);
     const NodeVal<T>* hp = sh + kNodes * p;
-    T dr = 0, di = 0;
+    T a[NT], dr[NT], di[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      a[t] = Bh[t] * static_cast<T>(2 * (p0 + p) + 1);
+      dr[t] = di[t] = 0;
+    }
 #pragma unroll 1
     for (int j = 0; j < kNodes; ++j) {
-      const T u = fma(Bh, gk_node_c(T(0), j), a);
-      const T J = j0_hc(u);
       const NodeVal<T> v = hp[j];
-      kr = fma(J, v.kr, kr);
-      ki = fma(J, v.ki, ki);
-      dr = fma(J, v.dr, dr);
-      di = fma(J, v.di, di);
+      const T x = gk_node_c(T(0), j);
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const T J = j0_hc(fma(Bh[t], x, a[t]));
+        kr[t] = fma(J, v.kr, kr[t]);
+        ki[t] = fma(J, v.ki, ki[t]);
+        dr[t] = fma(J, v.dr, dr[t]);
+        di[t] = fma(J, v.di, di[t]);
+      }
     }
-    err += est_sqrt(dr * dr + di * di);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) err[t] += est_sqrt(dr[t] * dr[t] + di[t] * di[t]);
   }
 }
 
@@ -461,84 +480,105 @@ __device__ __forceinline__ float2 j0_pair_regime(float2 u) {
   return make_float2(u.x > kJ0Split ? Jl.x : Js.x, u.y > kJ0Split ? Jl.y : Js.y);
 }
 
-// Pair k of one FP32 panel in regime R: J0 at both nodes (x = node
-// coordinates), the Kronrod sums, the Gauss sum of the odd node.
-template <int R>
-__device__ __forceinline__ void panel_pair(float2 x, float4 v, float2 g, float Bh, float a,
-                                           float2& KR, float2& KI, float& gr, float& gi) {
-  const float2 u = make_float2(fmaf(x.x, Bh, a), fmaf(x.y, Bh, a));
-  const float2 J = j0_pair_regime<R>(u);
-  KR = __ffma2_rn(J, make_float2(v.x, v.y), KR);
-  KI = __ffma2_rn(J, make_float2(v.z, v.w), KI);
-  gr = fmaf(J.y, g.x, gr);
-  gi = fmaf(J.y, g.y, gi);
+// Pair k of one FP32 panel in regime R for each of the lane's NT taps: J0 at
+// both nodes (x = node coordinates), the Kronrod sums, the Gauss sum of the
+// odd node.  The node values v, g are loaded once for all NT taps.
+template <int R, int NT>
+__device__ __forceinline__ void panel_pair(float2 x, float4 v, float2 g, const float (&Bh)[NT],
+                                           const float (&a)[NT], float2 (&KR)[NT],
+                                           float2 (&KI)[NT], float (&gr)[NT], float (&gi)[NT]) {
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const float2 u = make_float2(fmaf(x.x, Bh[t], a[t]), fmaf(x.y, Bh[t], a[t]));
+    const float2 J = j0_pair_regime<R>(u);
+    KR[t] = __ffma2_rn(J, make_float2(v.x, v.y), KR[t]);
+    KI[t] = __ffma2_rn(J, make_float2(v.z, v.w), KI[t]);
+    gr[t] = fmaf(J.y, g.x, gr[t]);
+    gi[t] = fmaf(J.y, g.y, gi[t]);
+  }
 }
 
 // Pairs [k0, k1) of one FP32 panel in regime R, in a rolled loop (node
 // coordinates from constant memory, values by computed index).
-template <int R>
-__device__ __forceinline__ void panel_pair_range(const float4* hp, int k0, int k1, float Bh,
-                                                 float a, float2& KR, float2& KI, float& gr,
-                                                 float& gi) {
+template <int R, int NT>
+__device__ __forceinline__ void panel_pair_range(const float4* hp, int k0, int k1,
+                                                 const float (&Bh)[NT], const float (&a)[NT],
+                                                 float2 (&KR)[NT], float2 (&KI)[NT],
+                                                 float (&gr)[NT], float (&gi)[NT]) {
   const float2* hg = reinterpret_cast<const float2*>(hp + 15);
 #pragma unroll 1
   for (int k = k0; k < k1; ++k)
-    panel_pair<R>(make_float2(c_gk_node_f[2 * k], c_gk_node_f[2 * k + 1]), hp[k], hg[k], Bh, a,
-                  KR, KI, gr, gi);
+    panel_pair<R, NT>(make_float2(c_gk_node_f[2 * k], c_gk_node_f[2 * k + 1]), hp[k], hg[k], Bh,
+                      a, KR, KI, gr, gi);
 }
 
-// One FP32 panel.  kAllFar = kPairFarthest or kPairFar: every pair is in
-// that regime (degree 1 or 2, unrolled); kAllFar = 0: pair k's regime follows from the warp-uniform counts ks (pairs
+// One FP32 panel for the lane's NT taps.  kAllFar = kPairFarthest or
+// kPairFar: every pair is in that regime (degree 1 or 2, unrolled);
+// kAllFar = 0: pair k's regime follows from the warp-uniform counts ks (pairs
 // all below the split), kn (pairs not all past it) and kf (pairs not all
 // past kJ0Far), ks <= kn <= kf: the small-argument series below ks, both
-// formulas below kn, degree 4 up to kf, degree 2 beyond.  Returns the
-// panel's Kronrod sum (kr, ki) and Gauss sum (gr, gi).
-template <int kAllFar>
-__device__ __forceinline__ void panel_sums(const float4* hp, float Bh, float a, int ks, int kn,
-                                           int kf, float& kr, float& ki, float& gr, float& gi) {
-  float2 KR = make_float2(0.f, 0.f), KI = KR;
-  gr = gi = 0.f;
+// formulas below kn, degree 4 up to kf, degree 2 beyond, in short rolled
+// loops.  Returns each tap's panel Kronrod sum (kr, ki) and Gauss sum (gr, gi).
+template <int kAllFar, int NT>
+__device__ __forceinline__ void panel_sums(const float4* hp, const float (&Bh)[NT],
+                                           const float (&a)[NT], int ks, int kn, int kf,
+                                           float (&kr)[NT], float (&ki)[NT], float (&gr)[NT],
+                                           float (&gi)[NT]) {
+  float2 KR[NT], KI[NT];
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    KR[t] = KI[t] = make_float2(0.f, 0.f);
+    gr[t] = gi[t] = 0.f;
+  }
   if (kAllFar) {
     const float2* hg = reinterpret_cast<const float2*>(hp + 15);
 #pragma unroll
     for (int k = 0; k < kPairs; ++k)
-      panel_pair<kAllFar == kPairFarthest ? kPairFarthest : kPairFar>(
+      panel_pair<kAllFar == kPairFarthest ? kPairFarthest : kPairFar, NT>(
           make_float2(static_cast<float>(gk_node(2 * k)), static_cast<float>(gk_node(2 * k + 1))),
           hp[k], hg[k], Bh, a, KR, KI, gr, gi);
   } else {
-    panel_pair_range<kPairSmall>(hp, 0, ks, Bh, a, KR, KI, gr, gi);
-    panel_pair_range<kPairBoth>(hp, ks, kn, Bh, a, KR, KI, gr, gi);
-    panel_pair_range<kPairNear>(hp, kn, kf, Bh, a, KR, KI, gr, gi);
-    panel_pair_range<kPairFar>(hp, kf, kPairs, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairSmall, NT>(hp, 0, ks, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairBoth, NT>(hp, ks, kn, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairNear, NT>(hp, kn, kf, Bh, a, KR, KI, gr, gi);
+    panel_pair_range<kPairFar, NT>(hp, kf, kPairs, Bh, a, KR, KI, gr, gi);
   }
   // node 30, the panel's last
-  const float u = fmaf(static_cast<float>(gk_node(kNodes - 1)), Bh, a);
-  const float J = kAllFar == kPairFarthest ? j0_farthest(u)
-                  : (kAllFar || kf < kPairs) ? j0_far(u) : j0_halfcycles(u);
   const float4 c = hp[23];
-  kr = fmaf(J, c.x, KR.x + KR.y);
-  ki = fmaf(J, c.y, KI.x + KI.y);
+#pragma unroll
+  for (int t = 0; t < NT; ++t) {
+    const float u = fmaf(static_cast<float>(gk_node(kNodes - 1)), Bh[t], a[t]);
+    const float J = kAllFar == kPairFarthest ? j0_farthest(u)
+                    : (kAllFar || kf < kPairs) ? j0_far(u) : j0_halfcycles(u);
+    kr[t] = fmaf(J, c.x, KR[t].x + KR[t].y);
+    ki[t] = fmaf(J, c.y, KI[t].x + KI[t].y);
+  }
 }
 
-// FP32: per panel, the Kronrod sum K_p and the Gauss sum G_p; the estimate
-// adds |K_p - G_p|, formed from the panel's own sums (of the panel's size,
-// not the whole integral's).  The J0 regime of each node pair follows from
-// the smallest and largest Bh of the warp's active lanes (warp-uniform):
-// node j of panel P lies at u = Bh (2 P + 1 + x_j) for each lane.
-__device__ __forceinline__ void eval_panels(const NodeVal<float>* sh, int p0, int np, float Bh,
-                                            float bh_min, float bh_max, bool active, float& kr,
-                                            float& ki, float& err) {
+// FP32: per panel, the Kronrod sum K_p and the Gauss sum G_p of each of the
+// lane's NT taps; the estimate adds |K_p - G_p|, formed from the panel's own
+// sums (of the panel's size, not the whole integral's).  The J0 regime of
+// each node pair follows from the smallest and largest Bh of the warp's
+// active taps (warp-uniform): node j of panel P lies at u = Bh (2 P + 1 + x_j)
+// for each tap.
+template <int NT>
+__device__ __forceinline__ void eval_panels_f32(const NodeVal<float>* sh, int p0, int np,
+                                                const float (&Bh)[NT], float bh_min,
+                                                float bh_max, float (&kr)[NT], float (&ki)[NT],
+                                                float (&err)[NT]) {
   const float4* hp = reinterpret_cast<const float4*>(sh);
   const int lane = threadIdx.x & 31;
   float f = static_cast<float>(2 * p0 + 1);   // 2 (p0 + p) + 1, exact
   for (int p = 0; p < np; ++p, f += 2.f, hp += kSlots) {
-    const float a = Bh * f;
-    float pkr, pki, pgr, pgi;
-    const float lo_min = bh_min * (f + c_gk_node_f[0]);   // lowest node of any lane
+    float a[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) a[t] = Bh[t] * f;
+    float pkr[NT], pki[NT], pgr[NT], pgi[NT];
+    const float lo_min = bh_min * (f + c_gk_node_f[0]);   // lowest node of any tap
     if (lo_min >= kJ0Farthest) {
-      panel_sums<kPairFarthest>(hp, Bh, a, 0, 0, 0, pkr, pki, pgr, pgi);
+      panel_sums<kPairFarthest, NT>(hp, Bh, a, 0, 0, 0, pkr, pki, pgr, pgi);
     } else if (lo_min >= kJ0Far) {
-      panel_sums<kPairFar>(hp, Bh, a, 0, 0, 0, pkr, pki, pgr, pgi);
+      panel_sums<kPairFar, NT>(hp, Bh, a, 0, 0, 0, pkr, pki, pgr, pgi);
     } else {
       // lane k < 15 classifies pair k; the counts are the same in every lane
       const bool on = lane < kPairs;
@@ -547,22 +587,157 @@ __device__ __forceinline__ void eval_panels(const NodeVal<float>* sh, int p0, in
       const int kf = __popc(__ballot_sync(0xffffffffu, on && !(bh_min * tlo >= kJ0Far)));
       const int kn = __popc(__ballot_sync(0xffffffffu, on && !(bh_min * tlo > kJ0Split)));
       const int ks = __popc(__ballot_sync(0xffffffffu, on && bh_max * thi <= kJ0Split));
-      panel_sums<0>(hp, Bh, a, ks, kn, kf, pkr, pki, pgr, pgi);
+      panel_sums<0, NT>(hp, Bh, a, ks, kn, kf, pkr, pki, pgr, pgi);
     }
-    kr += pkr;
-    ki += pki;
-    const float dr = pkr - pgr, di = pki - pgi;
-    err += est_sqrt(dr * dr + di * di);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      kr[t] += pkr[t];
+      ki[t] += pki[t];
+      const float dr = pkr[t] - pgr[t], di = pki[t] - pgi[t];
+      err[t] += est_sqrt(dr * dr + di * di);
+    }
+  }
+}
+
+// The FP32 quadrature of eval_chunk for NT taps per lane (a chunk of 32 NT
+// taps): one node build, one panel schedule and one refinement decision for
+// all of them.
+template <int NT, typename N>
+__device__ __forceinline__ void eval_chunk_f32(NodeVal<float>* sh, const QuadParams& q,
+                                               const float (&rho)[NT], const bool (&active)[NT],
+                                               double dw, int npan, int max_panels, int& built,
+                                               bool (&ok)[NT], int lane, N& nodes,
+                                               float2 (&K)[NT]) {
+  npan = min(npan, max_panels);
+  // the active taps' extreme radii (warp-uniform)
+  float rmin = 1e30f, rmax = 0.f;
+#pragma unroll
+  for (int t = 0; t < NT; ++t)
+    if (active[t]) {
+      rmin = fminf(rmin, rho[t]);
+      rmax = fmaxf(rmax, rho[t]);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    rmin = fminf(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
+    rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+  }
+  int refine = 0;
+  while (true) {
+    const float hb = q.Rf / static_cast<float>(npan);
+    float Bh[NT], kr[NT], ki[NT], err[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      nodes += active[t] ? static_cast<N>(kNodes * npan) : N(0);
+      Bh[t] = hb * rho[t];
+      kr[t] = ki[t] = err[t] = 0.f;
+    }
+    if (npan <= kPanelBatch) {
+      if (built != npan) {
+        __syncwarp();
+        build_nodes(sh, q, npan, 0, npan, dw, lane);
+        __syncwarp();
+        built = npan;
+      }
+      eval_panels_f32<NT>(sh, 0, npan, Bh, hb * rmin, hb * rmax, kr, ki, err);
+    } else {
+      for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
+        const int nb = min(kPanelBatch, npan - p0);
+        __syncwarp();
+        build_nodes(sh, q, npan, p0, nb, dw, lane);
+        __syncwarp();
+        eval_panels_f32<NT>(sh, p0, nb, Bh, hb * rmin, hb * rmax, kr, ki, err);
+      }
+      built = 0;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const float lim = fmaxf(q.tol_abs, q.tol_rel * est_sqrt(kr[t] * kr[t] + ki[t] * ki[t]));
+      ok[t] = (!active[t]) || err[t] <= lim;
+      bad = bad || !ok[t];
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    if (!any_bad || refine >= q.max_refine || npan >= max_panels) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) K[t] = make_float2(kr[t], ki[t]);
+      return;
+    }
+    ++refine;
+    npan = min(2 * npan, max_panels);
   }
 }
 
 // Half-cycles of J0 per unit node coordinate for a tap at rho on npan
-// panels: 2 rho R / (2 npan).
-__device__ __forceinline__ float panel_bh(const QuadParams& q, float rho, int npan) {
-  return (q.Rf / static_cast<float>(npan)) * rho;
-}
+// panels: 2 rho R / (2 npan) (the FP32 path forms (R / npan) rho in FP32).
 __device__ __forceinline__ double panel_bh(const QuadParams& q, double rho, int npan) {
   return (q.R / npan) * rho;
+}
+
+// eval_chunk's FP64 path for NT taps per lane: one NodeVal per node.
+template <int NT, typename T, typename C, typename N>
+__device__ __forceinline__ void eval_chunk_generic(NodeVal<T>* sh, const QuadParams& q,
+                                                   const T (&rho)[NT], const bool (&active)[NT],
+                                                   double dw, int npan, int max_panels,
+                                                   int& built, bool (&ok)[NT], int lane,
+                                                   N& nodes, C (&K)[NT]) {
+  npan = min(npan, max_panels);
+  int refine = 0;
+  while (true) {
+    T Bh[NT], kr[NT], ki[NT], err[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      nodes += active[t] ? static_cast<N>(kNodes * npan) : N(0);
+      Bh[t] = panel_bh(q, rho[t], npan);
+      kr[t] = ki[t] = err[t] = 0;
+    }
+    if (npan <= kPanelBatch) {
+      if (built != npan) {
+        __syncwarp();
+        build_nodes(sh, q, npan, 0, npan, dw, lane);
+        __syncwarp();
+        built = npan;
+      }
+      eval_panels<T, NT>(sh, 0, npan, Bh, kr, ki, err);
+    } else {
+      for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
+        const int nb = min(kPanelBatch, npan - p0);
+        __syncwarp();
+        build_nodes(sh, q, npan, p0, nb, dw, lane);
+        __syncwarp();
+        eval_panels<T, NT>(sh, p0, nb, Bh, kr, ki, err);
+      }
+      built = 0;
+    }
+    bool bad = false;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const T lim = fmax(static_cast<T>(q.tol_abs),
+                         static_cast<T>(q.tol_rel) * est_sqrt(kr[t] * kr[t] + ki[t] * ki[t]));
+      ok[t] = (!active[t]) || err[t] <= lim;
+      bad = bad || !ok[t];
+    }
+    const bool any_bad = __any_sync(0xffffffffu, bad);
+    if (!any_bad || refine >= q.max_refine || npan >= max_panels) {
+#pragma unroll
+      for (int t = 0; t < NT; ++t) K[t] = cmake<C>(kr[t], ki[t]);
+      return;
+    }
+    ++refine;
+    npan = min(2 * npan, max_panels);
+  }
+}
+
+// [GC] for NT taps per lane of a chunk of 32 NT taps, in the precision T.
+template <int NT, typename T, typename C, typename N>
+__device__ __forceinline__ void eval_chunk_nt(NodeVal<T>* sh, const QuadParams& q,
+                                              const T (&rho)[NT], const bool (&active)[NT],
+                                              double dw, int npan, int max_panels, int& built,
+                                              bool (&ok)[NT], int lane, N& nodes, C (&K)[NT]) {
+  if constexpr (sizeof(T) == 4)
+    eval_chunk_f32<NT>(sh, q, rho, active, dw, npan, max_panels, built, ok, lane, nodes, K);
+  else
+    eval_chunk_generic<NT>(sh, q, rho, active, dw, npan, max_panels, built, ok, lane, nodes, K);
 }
 
 // Evaluate [GC](rho, dw) for one tap per lane (inactive lanes compute a
@@ -574,45 +749,13 @@ template <typename T, typename C, typename N>
 __device__ __forceinline__ C eval_chunk(NodeVal<T>* sh, const QuadParams& q, T rho, bool active,
                                         double dw, int npan, int max_panels, int& built, bool& ok,
                                         int lane, N& nodes) {
-  npan = min(npan, max_panels);
-  // the active lanes' extreme radii (warp-uniform)
-  T rmin = active ? rho : T(1e30), rmax = active ? rho : T(0);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    rmin = fmin(rmin, __shfl_xor_sync(0xffffffffu, rmin, o));
-    rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-  }
-  int refine = 0;
-  while (true) {
-    nodes += active ? static_cast<N>(kNodes * npan) : N(0);
-    const T Bh = panel_bh(q, rho, npan);
-    const T bmin = panel_bh(q, rmin, npan), bmax = panel_bh(q, rmax, npan);
-    T kr = 0, ki = 0, err = 0;
-    if (npan <= kPanelBatch) {
-      if (built != npan) {
-        __syncwarp();
-        build_nodes(sh, q, npan, 0, npan, dw, lane);
-        __syncwarp();
-        built = npan;
-      }
-      eval_panels(sh, 0, npan, Bh, bmin, bmax, active, kr, ki, err);
-    } else {
-      for (int p0 = 0; p0 < npan; p0 += kPanelBatch) {
-        const int nb = min(kPanelBatch, npan - p0);
-        __syncwarp();
-        build_nodes(sh, q, npan, p0, nb, dw, lane);
-        __syncwarp();
-        eval_panels(sh, p0, nb, Bh, bmin, bmax, active, kr, ki, err);
-      }
-      built = 0;
-    }
-    const T lim = fmax(static_cast<T>(q.tol_abs), static_cast<T>(q.tol_rel) * est_sqrt(kr * kr + ki * ki));
-    ok = (!active) || err <= lim;
-    const bool any_bad = __any_sync(0xffffffffu, !ok);
-    if (!any_bad || refine >= q.max_refine || npan >= max_panels) return cmake<C>(kr, ki);
-    ++refine;
-    npan = min(2 * npan, max_panels);
-  }
+  const T r1[1] = {rho};
+  const bool a1[1] = {active};
+  bool ok1[1];
+  C K1[1];
+  eval_chunk_nt<1>(sh, q, r1, a1, dw, npan, max_panels, built, ok1, lane, nodes, K1);
+  ok = ok1[0];
+  return K1[0];
 }
 
 // ---------------------------------------------------------------------------
@@ -709,18 +852,26 @@ __device__ __forceinline__ int initial_panels(const QuadParams& q, float rho_max
   return panel_count_for(q.Rf * fmaf(adw, q.chirp_coeff, rho_max) * q.inv_cycles);
 }
 
+// Taps per lane of the fused kernel's chunks.
+constexpr int kVisTaps = 2;
+
+// Block shape of the fused kernel: threads per block and the blocks per SM
+// its register budget is sized for (FP32: 4 x 256 threads, 64 registers;
+// 7 x 128 threads at 72 registers and 3 x 256 at 80 ran slower).
+template <typename T> struct VisLaunch {
+  static constexpr int threads = 256;
+  static constexpr int min_blocks = sizeof(T) == 4 ? 4 : 2;
+};
+
 // One warp per visibility, visibilities taken from a work queue.  Taps are
-// visited in order of distance from the box centre, 32 at a time; each
-// chunk takes the panel count its farthest tap needs.
+// visited in order of distance from the box centre, 32 kVisTaps at a time;
+// each chunk takes the panel count its farthest tap needs.
 template <typename T, typename C, bool kGrid>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const VisRec<T>* __restrict__ recs,
-                                                     const uint32_t* __restrict__ perm, int64_t n,
-                                                     const C* __restrict__ grid_in, C* grid_out,
-                                                     const C* __restrict__ vis_in,
-                                                     C* __restrict__ vis_out, QuadParams q,
-                                                     const int32_t* __restrict__ stack_slot,
-                                                     unsigned long long* head,
-                                                     unsigned long long* stats, int batch) {
+__global__ void __launch_bounds__(VisLaunch<T>::threads, VisLaunch<T>::min_blocks)
+    vis_kernel(const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
+               const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
+               C* __restrict__ vis_out, QuadParams q, const int32_t* __restrict__ stack_slot,
+               unsigned long long* head, unsigned long long* stats, int batch) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -744,28 +895,41 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_kernel(const 
                        : cmake<C>(0.0, 0.0);
     C accv = cmake<C>(0.0, 0.0);
     const int ntap = Jw * Jw;
-    for (int t0 = 0; t0 < ntap; t0 += 32) {
-      const int t = t0 + lane;
-      const bool active = t < ntap;
-      const uint32_t code = order[active ? t : 0];
-      const int ou = static_cast<int>(code & 0xffu) - half + 1;
-      const int ov = static_cast<int>(code >> 8) - half + 1;
-      const T du_ = fu - static_cast<T>(ou), dv_ = fv - static_cast<T>(ov);
-      const T rho = sqrt(du_ * du_ + dv_ * dv_);
-      T rmax = active ? rho : T(0);
+    // kVisTaps taps per lane: a chunk of 32 kVisTaps consecutive taps shares
+    // one node build, panel schedule and refinement decision
+    for (int t0 = 0; t0 < ntap; t0 += 32 * kVisTaps) {
+      T rho[kVisTaps];
+      bool act[kVisTaps], ok[kVisTaps];
+      uint32_t code[kVisTaps];
+      T rmax = T(0);
+#pragma unroll
+      for (int k = 0; k < kVisTaps; ++k) {
+        const int t = t0 + 32 * k + lane;
+        act[k] = t < ntap;
+        code[k] = order[act[k] ? t : 0];
+        const T du_ = fu - static_cast<T>(static_cast<int>(code[k] & 0xffu) - half + 1);
+        const T dv_ = fv - static_cast<T>(static_cast<int>(code[k] >> 8) - half + 1);
+        rho[k] = sqrt(du_ * du_ + dv_ * dv_);
+        if (act[k]) rmax = fmax(rmax, rho[k]);
+      }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
       const int npan = initial_panels(q, static_cast<float>(rmax), adw);
-      bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, kMaxPanels, built, ok, lane, my_nodes);
-      if (active) {
-        ++my_taps;
-        if (!ok) ++my_bad;
-        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
-                           wrap_index(r.bu + ou, npad);
-        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
-      }
+      C K[kVisTaps];
+      eval_chunk_nt<kVisTaps>(sh, q, rho, act, r.dw, npan, kMaxPanels, built, ok, lane, my_nodes,
+                              K);
+#pragma unroll
+      for (int k = 0; k < kVisTaps; ++k)
+        if (act[k]) {
+          if (!ok[k]) ++my_bad;
+          const int ou = static_cast<int>(code[k] & 0xffu) - half + 1;
+          const int ov = static_cast<int>(code[k] >> 8) - half + 1;
+          const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                             wrap_index(r.bu + ou, npad);
+          apply_tap<C, kGrid>(K[k], gi, yv, grid_in, grid_out, accv);
+        }
     }
+    if (lane == 0) my_taps += static_cast<unsigned long long>(ntap);
     if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
   flush_counts(stats, my_bad, my_taps, my_nodes, lane);
@@ -807,17 +971,142 @@ __global__ void __launch_bounds__(256) table_sample_kernel(C* __restrict__ raw, 
   }
 }
 
+// Pair entries for w-row j at radius i: {K(j, i), K(j + 1, i) - K(j, i)}.
 template <typename C>
 __global__ void table_pair_kernel(const C* __restrict__ raw, int64_t nr, int64_t nw,
                                   KPair<C>* __restrict__ pairs) {
   const int64_t total = (nw - 1) * nr;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total;
        k += (int64_t)gridDim.x * blockDim.x) {
+    const C lo = raw[k], hi = raw[k + nr];
     KPair<C> v;
-    v.a = raw[k];
-    v.b = raw[k + nr];
+    v.a = lo;
+    v.b.x = hi.x - lo.x;
+    v.b.y = hi.y - lo.y;
     pairs[k] = v;
   }
+}
+
+// The tabulated kernel between radius samples i (p0) and i + 1 (p1) at
+// fractions fr (radius) and fw (w-row): linear in |dw| at each radius, then
+// linear in rho.
+template <typename T, typename C>
+__device__ __forceinline__ C table_interp(const KPair<C>& p0, const KPair<C>& p1, T fr, T fw) {
+  const T k0x = fma(fw, p0.b.x, p0.a.x), k0y = fma(fw, p0.b.y, p0.a.y);
+  const T k1x = fma(fw, p1.b.x, p1.a.x), k1y = fma(fw, p1.b.y, p1.a.y);
+  C K;
+  K.x = fma(fr, k1x - k0x, k0x);
+  K.y = fma(fr, k1y - k0y, k0y);
+  return K;
+}
+
+// Table position of a tap at (du, dv) cells from the visibility: s =
+// |(du, dv)| / h_rho.  FP32 takes the hardware square root (relative error
+// about 2^-22, far below the table's interpolation error); FP64 the
+// correctly rounded one.
+__device__ __forceinline__ float table_radius(float du, float dv, float inv_hr) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(fmaf(du, du, dv * dv)));
+  return r * inv_hr;
+}
+__device__ __forceinline__ double table_radius(double du, double dv, double inv_hr) {
+  return sqrt(fma(du, du, dv * dv)) * inv_hr;
+}
+
+// The taps of one visibility from the plane pair of its w-row (`row`, in
+// shared or global memory), raster order, 32 at a time; tap t = b J_w + a is
+// advanced by 32 per step without a division, the offsets also kept as
+// floats so that no tap needs an int <-> float conversion (those run on the
+// FP64 unit here).  kContig: the box lies inside the grid without wrapping
+// (warp-uniform) and `grid` points at its first cell, so tap (a, b) is cell
+// b npad + a; otherwise `grid` is the stack's grid and each tap wraps its own
+// indices.  The conjugation for dw < 0 is left to the caller: with K = Kx +
+// i s Ky, degridding sums Kx g (sx) and Ky g (sy) apart, gridding adds
+// Kx yv + Ky ys with ys = -i s yv.
+template <bool kContig, bool kGrid, typename T, typename C>
+__device__ __forceinline__ void table_vis_taps(const KPair<C>* __restrict__ row,
+                                               const VisRec<T>& r, T fw, int nr, T inv_hr,
+                                               int npad, const C* __restrict__ grid_in,
+                                               C* grid_out, C yv, C ys, C& sx, C& sy,
+                                               int lane) {
+  const int Jw = r.jw, half = Jw / 2, ntap = Jw * Jw;
+  const T last_r = static_cast<T>(nr - 2);
+  int a = lane % Jw, b = lane / Jw;
+  const int step_b = 32 / Jw, step_a = 32 % Jw;
+  T du_ = r.fu - static_cast<T>(a - half + 1), dv_ = r.fv - static_cast<T>(b - half + 1);
+  const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
+  const T fJw = static_cast<T>(Jw);
+  int off = b * npad + a;
+  const int step_off = step_b * npad + step_a, carry_off = npad - Jw;
+#pragma unroll 4
+  for (int t0 = 0; t0 < ntap; t0 += 32) {
+    int ir;
+    T fr;
+    table_index(table_radius(du_, dv_, inv_hr), nr - 2, last_r, ir, fr);
+    const C K = table_interp<T, C>(row[ir], row[ir + 1], fr, fw);
+    int64_t gi;
+    if (kContig) {
+      gi = off;
+    } else {
+      gi = static_cast<int64_t>(wrap_index(r.bv + b - half + 1, npad)) * npad +
+           wrap_index(r.bu + a - half + 1, npad);
+    }
+    if (t0 + lane < ntap) {
+      if (kGrid) {
+        C add;
+        add.x = fma(K.x, yv.x, K.y * ys.x);
+        add.y = fma(K.x, yv.y, K.y * ys.y);
+        atomic_add_c(grid_out + gi, add);
+      } else {
+        const C g = grid_in[gi];
+        sx.x = fma(K.x, g.x, sx.x);
+        sx.y = fma(K.x, g.y, sx.y);
+        sy.x = fma(K.y, g.x, sy.x);
+        sy.y = fma(K.y, g.y, sy.y);
+      }
+    }
+    a += step_a;
+    b += step_b;
+    du_ -= fstep_a;
+    dv_ -= fstep_b;
+    off += step_off;
+    if (a >= Jw) {
+      a -= Jw;
+      ++b;
+      du_ += fJw;
+      dv_ -= T(1);
+      off += carry_off;
+    }
+  }
+}
+
+// One visibility of a table kernel: the box's placement on the grid, the
+// conjugation for dw < 0 and the tap loop; degridding returns the lane's
+// partial sum.
+template <bool kGrid, typename T, typename C>
+__device__ __forceinline__ C table_vis(const KPair<C>* __restrict__ row, const VisRec<T>& r,
+                                       T fw, int nr, T inv_hr, int npad,
+                                       const C* __restrict__ grid_in, C* grid_out, C yv,
+                                       int lane) {
+  const int Jw = r.jw, half = Jw / 2;
+  const T sg = r.dw < 0.0 ? T(-1) : T(1);
+  C ys;
+  ys.x = sg * yv.y;
+  ys.y = -sg * yv.x;
+  C sx = cmake<C>(0.0, 0.0), sy = cmake<C>(0.0, 0.0);
+  const int u0 = wrap_index(r.bu - half + 1, npad), v0 = wrap_index(r.bv - half + 1, npad);
+  if (u0 + Jw <= npad && v0 + Jw <= npad) {
+    const int64_t o0 = static_cast<int64_t>(v0) * npad + u0;
+    table_vis_taps<true, kGrid>(row, r, fw, nr, inv_hr, npad, kGrid ? nullptr : grid_in + o0,
+                                kGrid ? grid_out + o0 : nullptr, yv, ys, sx, sy, lane);
+  } else {
+    table_vis_taps<false, kGrid>(row, r, fw, nr, inv_hr, npad, grid_in, grid_out, yv, ys, sx,
+                                 sy, lane);
+  }
+  C acc;   // sum of (Kx + i s Ky) g
+  acc.x = fma(-sg, sy.y, sx.x);
+  acc.y = fma(sg, sy.x, sx.y);
+  return acc;
 }
 
 // Degrid / grid with every tap interpolated bilinearly in (rho, |dw|) from
@@ -844,60 +1133,18 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
   unsigned long long i;
   while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
     const VisRec<T> r = recs[i];
-    const int Jw = r.jw;
     // the grid of this visibility's stack within the resident group
     const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
-    const int half = Jw / 2;
-    const T fu = r.fu, fv = r.fv;
     const T aw = table_w_scaled(static_cast<T>(fabs(r.dw)), tv.inv_hw);
     const int jrow = table_w_row(aw, nw - 2);
     const T fw = aw - static_cast<T>(jrow);
-    const bool neg = r.dw < 0.0;
-    const KPair<C>* row = pairs + static_cast<int64_t>(jrow) * nr;
     const uint32_t pm = perm[i];
     const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
                        : cmake<C>(0.0, 0.0);
-    C accv = cmake<C>(0.0, 0.0);
-    const int ntap = Jw * Jw;
-    // Tap t = b Jw + a, advanced by 32 per chunk without a division per tap;
-    // the offsets are also kept as floats so that no tap needs an int <-> float
-    // conversion (those run on the FP64 unit here).
-    int a = lane % Jw, b = lane / Jw;
-    const int step_b = 32 / Jw, step_a = 32 % Jw;
-    T du_ = fu - static_cast<T>(a - half + 1), dv_ = fv - static_cast<T>(b - half + 1);
-    const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
-    const T fJw = static_cast<T>(Jw), last_r = static_cast<T>(nr - 2);
-    for (int t0 = 0; t0 < ntap; t0 += 32) {
-      const int t = t0 + lane;
-      if (t < ntap) {
-        const int ou = a - half + 1, ov = b - half + 1;
-        const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
-        int ir;
-        T fr;
-        table_index(sr, nr - 2, last_r, ir, fr);
-        const KPair<C> p0 = row[ir], p1 = row[ir + 1];
-        const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
-        const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
-        C K;
-        K.x = fma(fw, hi_x - lo_x, lo_x);
-        K.y = fma(fw, hi_y - lo_y, lo_y);
-        if (neg) K.y = -K.y;
-        ++my_taps;
-        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
-                           wrap_index(r.bu + ou, npad);
-        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
-      }
-      a += step_a;
-      b += step_b;
-      du_ -= fstep_a;
-      dv_ -= fstep_b;
-      if (a >= Jw) {
-        a -= Jw;
-        ++b;
-        du_ += fJw;
-        dv_ -= T(1);
-      }
-    }
+    const C accv = table_vis<kGrid>(pairs + static_cast<int64_t>(jrow) * nr, r, fw, nr,
+                                    tv.inv_hr, npad, kGrid ? nullptr : grid_in + gbase,
+                                    kGrid ? grid_out + gbase : nullptr, yv, lane);
+    if (lane == 0) my_taps += static_cast<unsigned long long>(r.jw * r.jw);
     if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
   flush_counts(stats, 0, my_taps, 0, lane);
@@ -974,18 +1221,11 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
       const T fJw = static_cast<T>(Jw);
       for (int t0 = 0; t0 < ntap; t0 += 32) {
         if (t0 + lane < ntap) {
-          const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
           int ir;
           T fr;
-          table_index(sr, nr - 2, last_r, ir, fr);
-          const KPair<C> p0 = row[ir], p1 = row[ir + 1];
-          const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
-          const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
-          C K;
-          K.x = fma(fw, hi_x - lo_x, lo_x);
-          K.y = fma(fw, hi_y - lo_y, lo_y);
+          table_index(table_radius(du_, dv_, tv.inv_hr), nr - 2, last_r, ir, fr);
+          C K = table_interp<T, C>(row[ir], row[ir + 1], fr, fw);
           if (neg) K.y = -K.y;
-          ++my_taps;
           const int li = (pv0 + b) * side + (pu0 + a);
           if (kGrid) {
             atomicAdd(&patch[li].x, K.x * yv.x + K.y * yv.y);   // conj(K) * yv
@@ -1007,6 +1247,7 @@ __global__ void __launch_bounds__(256) tile_table_kernel(
           dv_ -= T(1);
         }
       }
+      if (lane == 0) my_taps += static_cast<unsigned long long>(ntap);
       if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
     }
     __syncthreads();
@@ -1050,7 +1291,6 @@ __global__ void __launch_bounds__(256) row_table_kernel(
   const int nwarps = blockDim.x >> 5;
   const KPair<C>* __restrict__ pairs = static_cast<const KPair<C>*>(tv.pairs);
   const int nr = static_cast<int>(tv.nr);
-  const T last_r = static_cast<T>(nr - 2);
   unsigned long long my_taps = 0;
   while (true) {
     if (threadIdx.x == 0) s_item = static_cast<int>(atomicAdd(head, 1ULL));
@@ -1065,55 +1305,17 @@ __global__ void __launch_bounds__(256) row_table_kernel(
     for (int ri = r0 + warp; ri < r1; ri += nwarps) {
       const uint32_t rec = row_idx[ri];
       const VisRec<T> r = recs[rec];
-      const int Jw = r.jw;
       const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
-      const int half = Jw / 2;
-      const T fu = r.fu, fv = r.fv;
       // the item's row is this record's (the plan keyed it with the same
       // arithmetic), so fw lies in [0, 1]
       const T fw = table_w_scaled(static_cast<T>(fabs(r.dw)), tv.inv_hw) - static_cast<T>(jrow);
-      const bool neg = r.dw < 0.0;
       const uint32_t pm = perm[rec];
       const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
                          : cmake<C>(0.0, 0.0);
-      C accv = cmake<C>(0.0, 0.0);
-      const int ntap = Jw * Jw;
-      int a = lane % Jw, b = lane / Jw;
-      const int step_b = 32 / Jw, step_a = 32 % Jw;
-      T du_ = fu - static_cast<T>(a - half + 1), dv_ = fv - static_cast<T>(b - half + 1);
-      const T fstep_a = static_cast<T>(step_a), fstep_b = static_cast<T>(step_b);
-      const T fJw = static_cast<T>(Jw);
-      #pragma unroll 4
-      for (int t0 = 0; t0 < ntap; t0 += 32) {
-        if (t0 + lane < ntap) {
-          const int ou = a - half + 1, ov = b - half + 1;
-          const T sr = sqrt(du_ * du_ + dv_ * dv_) * tv.inv_hr;
-          int ir;
-          T fr;
-          table_index(sr, nr - 2, last_r, ir, fr);
-          const KPair<C> p0 = row[ir], p1 = row[ir + 1];
-          const T lo_x = fma(fr, p1.a.x - p0.a.x, p0.a.x), lo_y = fma(fr, p1.a.y - p0.a.y, p0.a.y);
-          const T hi_x = fma(fr, p1.b.x - p0.b.x, p0.b.x), hi_y = fma(fr, p1.b.y - p0.b.y, p0.b.y);
-          C K;
-          K.x = fma(fw, hi_x - lo_x, lo_x);
-          K.y = fma(fw, hi_y - lo_y, lo_y);
-          if (neg) K.y = -K.y;
-          ++my_taps;
-          const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
-                             wrap_index(r.bu + ou, npad);
-          apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
-        }
-        a += step_a;
-        b += step_b;
-        du_ -= fstep_a;
-        dv_ -= fstep_b;
-        if (a >= Jw) {
-          a -= Jw;
-          ++b;
-          du_ += fJw;
-          dv_ -= T(1);
-        }
-      }
+      const C accv = table_vis<kGrid>(row, r, fw, nr, tv.inv_hr, npad,
+                                      kGrid ? nullptr : grid_in + gbase,
+                                      kGrid ? grid_out + gbase : nullptr, yv, lane);
+      if (lane == 0) my_taps += static_cast<unsigned long long>(r.jw * r.jw);
       if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
     }
     __syncthreads();   // the row is rewritten by the next item
@@ -1310,7 +1512,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
       if (t < ntap) {
         const int ou = a - half + 1, ov = b - half + 1;
         const C K = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
-        ++my_taps;
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
         apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
@@ -1328,6 +1529,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
     }
     // the series storage is rewritten by the next visibility's samples
     __syncwarp();
+    if (lane == 0) my_taps += static_cast<unsigned long long>(ntap);
     if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
   flush_counts(stats, my_bad, my_taps, my_nodes, lane);
@@ -1460,7 +1662,7 @@ template <typename T, typename C>
 int blocks_for_vis(const Plan& p, size_t smem) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vis_kernel<T, C, false>,
-                                                    kVisThreads, smem) != cudaSuccess ||
+                                                    VisLaunch<T>::threads, smem) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
   return per_sm * p.num_sms;
@@ -1754,11 +1956,12 @@ int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C
         p.stack_slot_dev, p.counters + g, p.counters + p.K,
         queue_batch(nk, blocks * (kVisThreads / 32)));
   } else {
-    const size_t smem = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<T>);
+    constexpr int threads = VisLaunch<T>::threads;
+    const size_t smem = (threads / 32) * kNodeBatch * sizeof(NodeVal<T>);
     const int blocks = blocks_for_vis<T, C>(p, smem);
-    vis_kernel<T, C, kGrid><<<blocks, kVisThreads, smem, s>>>(
+    vis_kernel<T, C, kGrid><<<blocks, threads, smem, s>>>(
         recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(), p.stack_slot_dev,
-        p.counters + g, p.counters + p.K, queue_batch(nk, blocks * (kVisThreads / 32)));
+        p.counters + g, p.counters + p.K, queue_batch(nk, blocks * (threads / 32)));
   }
   PHI_CUDA_TRY(cudaGetLastError());
   return PHI_OK;
