@@ -71,15 +71,21 @@ def parse():
                          "1-D w-planes with bilinear interpolation (Sec. 5.1.1)")
     ap.add_argument("--table-tol", type=float, default=1e-4)
     ap.add_argument("--tile", type=int, default=32, help="uv tile side of the visibility sort")
-    ap.add_argument("--grid-staging", type=int, default=0, choices=[0, 1, 2],
+    ap.add_argument("--grid-staging", type=int, default=None, choices=[0, 1, 2],
                     help="table path: 0 one warp per visibility, 1 uv tiles staged in shared "
-                         "memory, 2 w-rows of the table staged in shared memory")
+                         "memory, 2 w-rows of the table staged in shared memory (default 2 "
+                         "with --kernel-mode table, else 0)")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"],
                     help="f32: FP32 path with FP64 chirp phase, quadrature tol 1e-6 (the "
                          "headline); f64: everything in FP64, quadrature tol 1e-12")
     ap.add_argument("--max-vis", type=int, default=0,
                     help="use only the first N visibilities (small profiling case)")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.grid_staging is None:
+        args.grid_staging = 2 if args.kernel_mode == "table" else 0
+    elif args.grid_staging and args.kernel_mode != "table":
+        ap.error("--grid-staging applies to --kernel-mode table only")
+    return args
 
 
 def dist_setup(args):
@@ -246,7 +252,7 @@ def profiled_pipes():
             vals[k.strip()] = v.strip()
     if vals.get("kernel_source_sha256") != kernel_source_hash():
         return None
-    keys = ("fma_heavy_pipe_pct", "fma_lite_pipe_pct", "issue_active_pct", "warp_inst_per_tap_node")
+    keys = ("fma_pipe_pct", "fma_heavy_pipe_pct", "issue_active_pct", "warp_inst_per_tap_node")
     out = {k: float(vals[k]) for k in keys if k in vals}
     out["source"] = "profiles/vis_kernel_degrid_mwa-2048-first40000_full.md (40,000-visibility case)"
     return out
@@ -539,13 +545,13 @@ def run_ours(args, ws, rank, local):
         tname = {0: "vis_table_kernel", 1: "tile_table_kernel", 2: "row_table_kernel"}[args.grid_staging]
         roof = {"bound": "hbm", "kernel": f"{tname} ({dom})", "achieved": ach_gbs,
                 "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
-                "traffic": profiled_traffic("table_" + dom),
+                "traffic": profiled_traffic("table_" + dom) if args.grid_staging == 2 else None,
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
                 "covered_grid_cells": cells,
                 "work_note": "records 32 B + permutation 4 B + visibility 8 B per visibility, "
                              "8 B per grid cell covered by a kernel box, the plane pairs once "
-                             "per launch; the kernel is L1/TEX bound (92% of that pipe in ncu), "
-                             "far below the HBM roofline"}
+                             "per launch; the kernel is bound by its shared-memory reads (L1/TEX "
+                             "86-94% busy in ncu for the w-row kernel), far below the HBM roofline"}
     elif args.kernel_mode == "radial":
         # executed work: the quadrature at the Chebyshev points (tap-nodes) and
         # the series evaluated at every tap; degrid and grid do the same work
@@ -889,7 +895,7 @@ def run_plan_study(args):
                            kernels_per_s=info["n_kept"] / rec["kernel_construction_s"])
                 plan.close()
                 if fold:
-                    for staged in (0, 1):
+                    for staged in (0, 1, 2):
                         tp = phi.Plan(uvw, image_n=n_img, fov_rad=math.radians(25.0), n_stacks=k,
                                       conj_fold=fold, max_support=256, kernel_mode="table",
                                       grid_staging=staged)
