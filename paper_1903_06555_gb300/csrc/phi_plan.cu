@@ -3,9 +3,9 @@
 // centres, drop test, support J_w, split of u/du into an integer base and a
 // fraction, sort by (stack, uv tile), per-pixel and per-node tables, cuFFT.
 //
-// All per-visibility work runs on the device.  The k-means sums are formed
-// deterministically (fixed block ranges, warp butterflies, fixed-order
-// combination), so a plan is bit-reproducible run to run.
+// All per-visibility work runs on the device.  The k-means sums are exact
+// integer sums of a fixed-point image of w, independent of their order, so a
+// plan is bit-reproducible run to run.
 #include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
@@ -15,6 +15,7 @@
 #include <new>
 
 #include "phi_internal.cuh"
+#include "kmeans_assign.cuh"
 #include "table_index.cuh"
 
 namespace phi {
@@ -65,97 +66,102 @@ __global__ void fold_kernel(const double* __restrict__ uvw, int64_t M, int fold,
   if (bad) atomicAdd(n_bad, bad);
 }
 
-// One sweep of Algorithm 1: nearest centre by (wbar_q - w_p)^2 (strict <, so
-// the lowest index wins ties) and per-block partial sums and counts per stack.
-// Block b owns the contiguous range [b*chunk, (b+1)*chunk); inside it each
-// warp takes 32 consecutive visibilities at a time and reduces every stack
-// present among them with a butterfly (lane 0's fixed order).
+// One sweep of Algorithm 1: every visibility's nearest centre, and per block
+// the fixed-point limb sums and member counts of each stack.  Block b owns
+// the contiguous range [b*chunk, (b+1)*chunk); each warp takes 32 consecutive
+// visibilities at a time, sums the limbs of every stack present among them
+// with warp reductions and adds them to the block's accumulators (integer
+// atomics: exact and order-independent).  `acc` = 0 skips the sums.
 __global__ void kmeans_sweep_kernel(const double* __restrict__ w, int64_t M, int64_t chunk,
-                                    const double* __restrict__ centres, int K,
-                                    int32_t* __restrict__ stack, double* __restrict__ part_sum,
-                                    double* __restrict__ part_cnt) {
-  extern __shared__ double sm[];
-  const int nwarps = blockDim.x >> 5;
-  double* c = sm;
-  double* wsum = sm + K;
-  double* wcnt = wsum + nwarps * K;
-  for (int q = threadIdx.x; q < K; q += blockDim.x) c[q] = centres[q];
-  for (int q = threadIdx.x; q < nwarps * K; q += blockDim.x) {
-    wsum[q] = 0.0;
-    wcnt[q] = 0.0;
+                                    const double* __restrict__ centres, int K, int S,
+                                    int32_t* __restrict__ stack,
+                                    unsigned long long* __restrict__ part) {
+  extern __shared__ unsigned long long sm_u64[];
+  unsigned long long* acc = sm_u64;                                  // [K][kAcc]
+  double* c = reinterpret_cast<double*>(acc + static_cast<size_t>(K) * kAcc);
+  float* cf = reinterpret_cast<float*>(c + K);
+  float* ce = cf + K;
+  for (int q = threadIdx.x; q < K; q += blockDim.x) {
+    const double cq = centres[q];
+    c[q] = cq;
+    cf[q] = static_cast<float>(cq);
+    ce[q] = km_centre_err(cf[q]);
   }
+  for (int q = threadIdx.x; q < K * kAcc; q += blockDim.x) acc[q] = 0ULL;
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
   const int64_t b0 = blockIdx.x * chunk;
   const int64_t b1 = min(M, b0 + chunk);
   for (int64_t base = b0 + 32 * (int64_t)warp; base < b1; base += 32 * (int64_t)nwarps) {
     const int64_t i = base + lane;
     const bool valid = i < b1;
-    double wi = 0.0;
-    int s = 0;  // also the stack of a non-finite w (every comparison fails)
+    int s = -1;
+    long long v = 0;
     if (valid) {
-      wi = w[i];
-      double best = INFINITY;
-      for (int q = 0; q < K; ++q) {
-        const double d = (c[q] - wi) * (c[q] - wi);
-        if (d < best) {
-          best = d;
-          s = q;
-        }
-      }
+      const double wi = w[i];
+      s = nearest_centre(wi, c, cf, ce, K);
       stack[i] = s;
+      v = w_fixed(wi, S);
     }
+    if (!part) continue;
     unsigned rem = __ballot_sync(0xffffffffu, valid);
     while (rem) {
-      const int leader = __ffs(rem) - 1;
-      const int sq = __shfl_sync(0xffffffffu, s, leader);
-      const unsigned mem = __ballot_sync(0xffffffffu, valid && s == sq);
-      double v = ((mem >> lane) & 1u) ? wi : 0.0;
+      const int sq = __shfl_sync(0xffffffffu, s, __ffs(rem) - 1);
+      const bool in = s == sq;
+      const unsigned mem = __ballot_sync(0xffffffffu, in);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) {
-        wsum[warp * K + sq] += v;
-        wcnt[warp * K + sq] += static_cast<double>(__popc(mem));
+      for (int l = 0; l < kLimbs; ++l) {
+        const unsigned t = __reduce_add_sync(0xffffffffu, in ? w_limb(v, l) : 0u);
+        if (lane == 0) atomicAdd(&acc[sq * kAcc + l], static_cast<unsigned long long>(t));
       }
+      if (lane == 0) atomicAdd(&acc[sq * kAcc + kLimbs], static_cast<unsigned long long>(__popc(mem)));
       rem &= ~mem;
     }
   }
+  if (!part) return;
   __syncthreads();
-  for (int q = threadIdx.x; q < K; q += blockDim.x) {
-    double s = 0.0, n = 0.0;
-    for (int wp = 0; wp < nwarps; ++wp) {
-      s += wsum[wp * K + q];
-      n += wcnt[wp * K + q];
-    }
-    part_sum[(int64_t)blockIdx.x * K + q] = s;
-    part_cnt[(int64_t)blockIdx.x * K + q] = n;
-  }
+  for (int q = threadIdx.x; q < K * kAcc; q += blockDim.x)
+    part[static_cast<int64_t>(blockIdx.x) * K * kAcc + q] = acc[q];
 }
 
-// Centre update: wbar_q = sum / count, or 0 for an empty stack (Algorithm 1),
-// and the convergence measure mean_q |new - old| / max(|old|, eps).
+// Centre update: one warp per stack sums the blocks' limb sums and counts
+// (exact integer sums), rebuilds the 96-bit fixed-point total, and sets
+// wbar_q = total 2^-S / count, or 0 for an empty stack (Algorithm 1); then
+// the convergence measure mean_q |new - old| / max(|old|, eps).
 // out[0..K) new centres, out[K..2K) counts, out[2K] measure.
-__global__ void kmeans_update_kernel(const double* __restrict__ part_sum,
-                                     const double* __restrict__ part_cnt, int nblocks, int K,
-                                     double eps, double* __restrict__ centres,
+__global__ void kmeans_update_kernel(const unsigned long long* __restrict__ part, int nblocks,
+                                     int K, int S, double eps, double* __restrict__ centres,
                                      double* __restrict__ out) {
-  __shared__ double rel[128];
-  const int q = threadIdx.x;
-  if (q < K) {
-    double s = 0.0, n = 0.0;
-    for (int b = 0; b < nblocks; ++b) {
-      s += part_sum[(int64_t)b * K + q];
-      n += part_cnt[(int64_t)b * K + q];
+  extern __shared__ double rel[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  for (int q = warp; q < K; q += nwarps) {
+    unsigned long long sum[kAcc];
+#pragma unroll
+    for (int l = 0; l < kAcc; ++l) sum[l] = 0ULL;
+    for (int b = lane; b < nblocks; b += 32) {
+      const unsigned long long* pb = part + (static_cast<int64_t>(b) * K + q) * kAcc;
+#pragma unroll
+      for (int l = 0; l < kAcc; ++l) sum[l] += pb[l];
     }
-    const double old = centres[q];
-    const double nc = n > 0.0 ? s / n : 0.0;
-    rel[q] = fabs(nc - old) / fmax(fabs(old), eps);
-    centres[q] = nc;
-    out[q] = nc;
-    out[K + q] = n;
+#pragma unroll
+    for (int l = 0; l < kAcc; ++l)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum[l] += __shfl_xor_sync(0xffffffffu, sum[l], o);
+    if (lane == 0) {
+      const double total = fixed_total(sum, S);
+      const double n = static_cast<double>(sum[kLimbs]);
+      const double old = centres[q];
+      const double nc = sum[kLimbs] > 0 ? total / n : 0.0;
+      rel[q] = fabs(nc - old) / fmax(fabs(old), eps);
+      centres[q] = nc;
+      out[q] = nc;
+      out[K + q] = n;
+    }
   }
   __syncthreads();
-  if (q == 0) {
+  if (threadIdx.x == 0) {
     double d = 0.0;
     for (int k = 0; k < K; ++k) d += rel[k];
     out[2 * K] = d / K;
@@ -439,7 +445,8 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   const int nblk = std::max(1, std::min<int>(p.num_sms * 4,
                                              static_cast<int>((M + kPlanThreads - 1) / kPlanThreads)));
   double *w_fold = nullptr, *pmin = nullptr, *pmax = nullptr, *centres = nullptr,
-         *psum = nullptr, *pcnt = nullptr, *upd = nullptr;
+         *upd = nullptr;
+  unsigned long long* part = nullptr;
   uint8_t* flag = nullptr;
   int32_t* stack = nullptr;
   PHI_CUDA_TRY(tmp.alloc(&w_fold, M));
@@ -448,8 +455,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   PHI_CUDA_TRY(tmp.alloc(&pmin, nblk));
   PHI_CUDA_TRY(tmp.alloc(&pmax, nblk));
   PHI_CUDA_TRY(tmp.alloc(&centres, K));
-  PHI_CUDA_TRY(tmp.alloc(&psum, static_cast<size_t>(nblk) * K));
-  PHI_CUDA_TRY(tmp.alloc(&pcnt, static_cast<size_t>(nblk) * K));
+  PHI_CUDA_TRY(tmp.alloc(&part, static_cast<size_t>(nblk) * K * kAcc));
   PHI_CUDA_TRY(tmp.alloc(&upd, 2 * K + 1));
 
   // --- fold and w range
@@ -481,22 +487,27 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   PHI_CUDA_TRY(cudaMemcpyAsync(centres, c.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
   std::vector<double> hupd(2 * K + 1);
   p.kmeans_sweeps = 0;
+  // fixed-point scale of the sums: |w| < 2^E for every w, so |w| 2^S < 2^62
+  int E = 0;
+  const double wabs = std::max(std::fabs(wmin), std::fabs(wmax));
+  if (wabs > 0.0) std::frexp(wabs, &E);
+  const int S = 62 - E;
+  const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
+  const size_t sweep_smem = static_cast<size_t>(K) * (kAcc * sizeof(unsigned long long) +
+                                                      sizeof(double) + 2 * sizeof(float));
   if (M > 0 && fixed_centres) {
-    const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
-    const size_t smem = sizeof(double) * (K + 2 * (kPlanThreads / 32) * K);
-    kmeans_sweep_kernel<<<nblk, kPlanThreads, smem, s>>>(w_fold, M, chunk, centres, K, stack, psum,
-                                                         pcnt);
+    kmeans_sweep_kernel<<<nblk, kPlanThreads, sweep_smem, s>>>(w_fold, M, chunk, centres, K, S,
+                                                               stack, nullptr);
     PHI_CUDA_TRY(cudaGetLastError());
     for (int q = 0; q < K; ++q) p.wbar[q] = c[q];
   } else if (M > 0) {
-    const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
-    const size_t smem = sizeof(double) * (K + 2 * (kPlanThreads / 32) * K);
     while (p.kmeans_sweeps < d.kmeans_max_iter) {
       ++p.kmeans_sweeps;
-      kmeans_sweep_kernel<<<nblk, kPlanThreads, smem, s>>>(w_fold, M, chunk, centres, K, stack,
-                                                           psum, pcnt);
+      kmeans_sweep_kernel<<<nblk, kPlanThreads, sweep_smem, s>>>(w_fold, M, chunk, centres, K, S,
+                                                                 stack, part);
       PHI_CUDA_TRY(cudaGetLastError());
-      kmeans_update_kernel<<<1, 128, 0, s>>>(psum, pcnt, nblk, K, eps, centres, upd);
+      kmeans_update_kernel<<<1, 32 * std::min(K, 32), sizeof(double) * K, s>>>(
+          part, nblk, K, S, eps, centres, upd);
       PHI_CUDA_TRY(cudaGetLastError());
       PHI_CUDA_TRY(cudaMemcpyAsync(hupd.data(), upd, sizeof(double) * (2 * K + 1),
                                    cudaMemcpyDeviceToHost, s));

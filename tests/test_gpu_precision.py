@@ -119,8 +119,8 @@ def test_fp32_error_estimate_decides_like_fp64():
     # The FP32 panel sums carry rounding of order 2^-24 sum_j |w_j h_j J_j|
     # (~6e-8 summed over the panels, against the 1e-6 tolerance), so a chunk
     # whose estimate lies within a few percent of the limit can be refined by
-    # one precision only: measured 1.2e-4 of the tap-nodes on this workload
-    # (about 25 of ~240,000 chunk decisions), FP32 the one refining more.  One
-    # differing decision moves ~31 npan x 32 tap-nodes (~5e-6 of the total);
-    # the bound allows about 200.
+    # one precision only: measured 1.5e-4 of the tap-nodes on this workload
+    # (64-tap chunks), FP32 the one refining more.  One differing decision
+    # moves ~31 npan x 64 tap-nodes (~1e-5 of the total); the bound allows
+    # about 100.
     assert abs(counts["f32"][2] - counts["f64"][2]) <= 1e-3 * counts["f64"][2]
