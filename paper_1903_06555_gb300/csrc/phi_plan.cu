@@ -25,6 +25,7 @@ int set_kernel_smem_limits();
 namespace {
 
 constexpr int kPlanThreads = 256;
+constexpr int kSweepBatch = 8;   // k-means sweeps launched per host round trip
 
 // Fold and extract w.  flag = 1 when the visibility was reflected.
 // Non-finite baselines are counted (the plan then refuses them).
@@ -69,16 +70,23 @@ __global__ void fold_kernel(const double* __restrict__ uvw, int64_t M, int fold,
 // One sweep of Algorithm 1: every visibility's nearest centre, and per block
 // the fixed-point limb sums and member counts of each stack.  Block b owns
 // the contiguous range [b*chunk, (b+1)*chunk); each warp takes 32 consecutive
-// visibilities at a time, sums the limbs of every stack present among them
-// with warp reductions and adds them to the block's accumulators (integer
-// atomics: exact and order-independent).  `acc` = 0 skips the sums.
+// visibilities at a time (the next group's w loaded ahead), sums the limbs of
+// every stack present among them with warp reductions and adds them to its
+// own accumulators in shared memory (lane l holds limb l); the block adds
+// its warps' accumulators at the end.  Integer sums: exact and
+// order-independent.  `part` = 0 skips the sums; a set `*done` (the
+// iteration has converged) makes the launch a no-op.
 __global__ void kmeans_sweep_kernel(const double* __restrict__ w, int64_t M, int64_t chunk,
                                     const double* __restrict__ centres, int K, int S,
                                     int32_t* __restrict__ stack,
-                                    unsigned long long* __restrict__ part) {
+                                    unsigned long long* __restrict__ part,
+                                    const int* __restrict__ done) {
+  if (done && *done) return;
   extern __shared__ unsigned long long sm_u64[];
-  unsigned long long* acc = sm_u64;                                  // [K][kAcc]
-  double* c = reinterpret_cast<double*>(acc + static_cast<size_t>(K) * kAcc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  unsigned long long* wacc = sm_u64;                                 // [nwarps][K][kAcc]
+  double* c = reinterpret_cast<double*>(wacc + static_cast<size_t>(nwarps) * K * kAcc);
   float* cf = reinterpret_cast<float*>(c + K);
   float* ce = cf + K;
   for (int q = threadIdx.x; q < K; q += blockDim.x) {
@@ -87,52 +95,66 @@ __global__ void kmeans_sweep_kernel(const double* __restrict__ w, int64_t M, int
     cf[q] = static_cast<float>(cq);
     ce[q] = km_centre_err(cf[q]);
   }
-  for (int q = threadIdx.x; q < K * kAcc; q += blockDim.x) acc[q] = 0ULL;
+  for (int q = threadIdx.x; q < nwarps * K * kAcc; q += blockDim.x) wacc[q] = 0ULL;
   __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
+  unsigned long long* my = wacc + static_cast<size_t>(warp) * K * kAcc;
   const int64_t b0 = blockIdx.x * chunk;
   const int64_t b1 = min(M, b0 + chunk);
-  for (int64_t base = b0 + 32 * (int64_t)warp; base < b1; base += 32 * (int64_t)nwarps) {
+  const int64_t step = 32 * (int64_t)nwarps;
+  int64_t base = b0 + 32 * (int64_t)warp;
+  double wn = (base + lane < b1) ? w[base + lane] : 0.0;
+  for (; base < b1; base += step) {
     const int64_t i = base + lane;
     const bool valid = i < b1;
+    const double wi = wn;
+    if (base + step + lane < b1) wn = w[base + step + lane];
     int s = -1;
     long long v = 0;
     if (valid) {
-      const double wi = w[i];
       s = nearest_centre(wi, c, cf, ce, K);
       stack[i] = s;
       v = w_fixed(wi, S);
     }
     if (!part) continue;
+    unsigned limb[kLimbs];
+#pragma unroll
+    for (int l = 0; l < kLimbs; ++l) limb[l] = w_limb(v, l);
     unsigned rem = __ballot_sync(0xffffffffu, valid);
     while (rem) {
       const int sq = __shfl_sync(0xffffffffu, s, __ffs(rem) - 1);
       const bool in = s == sq;
       const unsigned mem = __ballot_sync(0xffffffffu, in);
+      unsigned mine = static_cast<unsigned>(__popc(mem));   // lane kLimbs: the count
 #pragma unroll
       for (int l = 0; l < kLimbs; ++l) {
-        const unsigned t = __reduce_add_sync(0xffffffffu, in ? w_limb(v, l) : 0u);
-        if (lane == 0) atomicAdd(&acc[sq * kAcc + l], static_cast<unsigned long long>(t));
+        const unsigned t = __reduce_add_sync(0xffffffffu, in ? limb[l] : 0u);
+        if (lane == l) mine = t;
       }
-      if (lane == 0) atomicAdd(&acc[sq * kAcc + kLimbs], static_cast<unsigned long long>(__popc(mem)));
+      if (lane < kAcc) my[sq * kAcc + lane] += mine;
       rem &= ~mem;
     }
   }
   if (!part) return;
   __syncthreads();
-  for (int q = threadIdx.x; q < K * kAcc; q += blockDim.x)
-    part[static_cast<int64_t>(blockIdx.x) * K * kAcc + q] = acc[q];
+  for (int q = threadIdx.x; q < K * kAcc; q += blockDim.x) {
+    unsigned long long t = 0;
+    for (int wp = 0; wp < nwarps; ++wp) t += wacc[static_cast<size_t>(wp) * K * kAcc + q];
+    part[static_cast<int64_t>(blockIdx.x) * K * kAcc + q] = t;
+  }
 }
 
 // Centre update: one warp per stack sums the blocks' limb sums and counts
 // (exact integer sums), rebuilds the 96-bit fixed-point total, and sets
 // wbar_q = total 2^-S / count, or 0 for an empty stack (Algorithm 1); then
 // the convergence measure mean_q |new - old| / max(|old|, eps).
-// out[0..K) new centres, out[K..2K) counts, out[2K] measure.
+// out[0..K) new centres, out[K..2K) counts, out[2K] measure.  state[0]
+// (done) is set once the measure falls below tol or state[1] (sweeps, counted
+// here) reaches max_iter; a launch after that is a no-op.
 __global__ void kmeans_update_kernel(const unsigned long long* __restrict__ part, int nblocks,
-                                     int K, int S, double eps, double* __restrict__ centres,
-                                     double* __restrict__ out) {
+                                     int K, int S, double eps, double tol, int max_iter,
+                                     double* __restrict__ centres, double* __restrict__ out,
+                                     int* __restrict__ state) {
+  if (state[0]) return;
   extern __shared__ double rel[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
@@ -164,7 +186,11 @@ __global__ void kmeans_update_kernel(const unsigned long long* __restrict__ part
   if (threadIdx.x == 0) {
     double d = 0.0;
     for (int k = 0; k < K; ++k) d += rel[k];
-    out[2 * K] = d / K;
+    d /= K;
+    out[2 * K] = d;
+    const int sweeps = state[1] + 1;
+    state[1] = sweeps;
+    if (d < tol || sweeps >= max_iter) state[0] = 1;
   }
 }
 
@@ -447,6 +473,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   double *w_fold = nullptr, *pmin = nullptr, *pmax = nullptr, *centres = nullptr,
          *upd = nullptr;
   unsigned long long* part = nullptr;
+  int* kstate = nullptr;   // k-means: done flag, sweeps
   uint8_t* flag = nullptr;
   int32_t* stack = nullptr;
   PHI_CUDA_TRY(tmp.alloc(&w_fold, M));
@@ -456,6 +483,7 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   PHI_CUDA_TRY(tmp.alloc(&pmax, nblk));
   PHI_CUDA_TRY(tmp.alloc(&centres, K));
   PHI_CUDA_TRY(tmp.alloc(&part, static_cast<size_t>(nblk) * K * kAcc));
+  PHI_CUDA_TRY(tmp.alloc(&kstate, 2));
   PHI_CUDA_TRY(tmp.alloc(&upd, 2 * K + 1));
 
   // --- fold and w range
@@ -493,27 +521,41 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   if (wabs > 0.0) std::frexp(wabs, &E);
   const int S = 62 - E;
   const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
-  const size_t sweep_smem = static_cast<size_t>(K) * (kAcc * sizeof(unsigned long long) +
-                                                      sizeof(double) + 2 * sizeof(float));
+  const size_t sweep_smem =
+      static_cast<size_t>(K) * ((kPlanThreads / 32) * kAcc * sizeof(unsigned long long) +
+                                sizeof(double) + 2 * sizeof(float));
+  PHI_CUDA_TRY(cudaFuncSetAttribute(kmeans_sweep_kernel,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    static_cast<int>(sweep_smem)));
   if (M > 0 && fixed_centres) {
     kmeans_sweep_kernel<<<nblk, kPlanThreads, sweep_smem, s>>>(w_fold, M, chunk, centres, K, S,
-                                                               stack, nullptr);
+                                                               stack, nullptr, nullptr);
     PHI_CUDA_TRY(cudaGetLastError());
     for (int q = 0; q < K; ++q) p.wbar[q] = c[q];
   } else if (M > 0) {
-    while (p.kmeans_sweeps < d.kmeans_max_iter) {
-      ++p.kmeans_sweeps;
-      kmeans_sweep_kernel<<<nblk, kPlanThreads, sweep_smem, s>>>(w_fold, M, chunk, centres, K, S,
-                                                                 stack, part);
+    // sweeps run in batches without a host round trip each: the update
+    // kernel sets the done flag, after which the batch's remaining launches
+    // return at once
+    PHI_CUDA_TRY(cudaMemsetAsync(kstate, 0, 2 * sizeof(int), s));
+    int hstate[2] = {0, 0};
+    int launched = 0;
+    while (!hstate[0] && launched < d.kmeans_max_iter) {
+      const int batch = std::min(kSweepBatch, d.kmeans_max_iter - launched);
+      for (int b = 0; b < batch; ++b) {
+        kmeans_sweep_kernel<<<nblk, kPlanThreads, sweep_smem, s>>>(w_fold, M, chunk, centres, K,
+                                                                   S, stack, part, kstate);
+        kmeans_update_kernel<<<1, 32 * std::min(K, 32), sizeof(double) * K, s>>>(
+            part, nblk, K, S, eps, d.kmeans_tol, d.kmeans_max_iter, centres, upd, kstate);
+      }
       PHI_CUDA_TRY(cudaGetLastError());
-      kmeans_update_kernel<<<1, 32 * std::min(K, 32), sizeof(double) * K, s>>>(
-          part, nblk, K, S, eps, centres, upd);
-      PHI_CUDA_TRY(cudaGetLastError());
-      PHI_CUDA_TRY(cudaMemcpyAsync(hupd.data(), upd, sizeof(double) * (2 * K + 1),
-                                   cudaMemcpyDeviceToHost, s));
+      launched += batch;
+      PHI_CUDA_TRY(cudaMemcpyAsync(hstate, kstate, sizeof(hstate), cudaMemcpyDeviceToHost, s));
       PHI_CUDA_TRY(cudaStreamSynchronize(s));
-      if (hupd[2 * K] < d.kmeans_tol) break;
     }
+    p.kmeans_sweeps = hstate[1];
+    PHI_CUDA_TRY(cudaMemcpyAsync(hupd.data(), upd, sizeof(double) * (2 * K + 1),
+                                 cudaMemcpyDeviceToHost, s));
+    PHI_CUDA_TRY(cudaStreamSynchronize(s));
     for (int q = 0; q < K; ++q) p.wbar[q] = hupd[q];
   } else {
     for (int q = 0; q < K; ++q) p.wbar[q] = c[q];
