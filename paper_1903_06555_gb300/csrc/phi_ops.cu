@@ -1448,22 +1448,36 @@ __device__ __forceinline__ C radial_eval(const C* ser, const RadialView<T>& rv, 
   const T x2 = x + x;
   const C* c = ser + ip * NS;
   // Clenshaw: b_m = 2 x b_{m+1} - b_{m+2} + c_m;  K = x b_1 - b_2 + c_0
-  T b1x = 0, b1y = 0, b2x = 0, b2y = 0;
+  if constexpr (sizeof(T) == 4) {
+    // real and imaginary parts side by side in paired FP32 operations (the
+    // same correctly rounded adds and multiply-adds as the scalar form)
+    const float2 xx = make_float2(x2, x2);
+    float2 b1 = make_float2(0.f, 0.f), b2 = make_float2(0.f, 0.f);
 #pragma unroll
-  for (int m = NC - 1; m >= 1; --m) {
-    const C cm = c[m];
-    const T nx = fma(x2, b1x, cm.x - b2x);
-    const T ny = fma(x2, b1y, cm.y - b2y);
-    b2x = b1x;
-    b2y = b1y;
-    b1x = nx;
-    b1y = ny;
+    for (int m = NC - 1; m >= 1; --m) {
+      const float2 nb = __ffma2_rn(xx, b1, __fadd2_rn(c[m], make_float2(-b2.x, -b2.y)));
+      b2 = b1;
+      b1 = nb;
+    }
+    return __ffma2_rn(make_float2(x, x), b1, __fadd2_rn(c[0], make_float2(-b2.x, -b2.y)));
+  } else {
+    T b1x = 0, b1y = 0, b2x = 0, b2y = 0;
+#pragma unroll
+    for (int m = NC - 1; m >= 1; --m) {
+      const C cm = c[m];
+      const T nx = fma(x2, b1x, cm.x - b2x);
+      const T ny = fma(x2, b1y, cm.y - b2y);
+      b2x = b1x;
+      b2y = b1y;
+      b1x = nx;
+      b1y = ny;
+    }
+    const C c0 = c[0];
+    C K;
+    K.x = fma(x, b1x, c0.x - b2x);
+    K.y = fma(x, b1y, c0.y - b2y);
+    return K;
   }
-  const C c0 = c[0];
-  C K;
-  K.x = fma(x, b1x, c0.x - b2x);
-  K.y = fma(x, b1y, c0.y - b2y);
-  return K;
 }
 
 // The radial mode's fused kernel: the series of each visibility, then every
