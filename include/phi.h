@@ -129,7 +129,26 @@ typedef struct {
                                index of the records sorted by stack and
                                w-row; falls back to 0 when a row exceeds a
                                block's shared memory) */
-  int32_t reserved0;        /* must be 0                                     */
+  int32_t grid_deterministic; /* 0 = gridding adds FP values with FP atomics
+                               (default; the order of the additions, and so
+                               the last bits of the grid, vary from run to
+                               run); 1 = every gridding contribution is
+                               rounded to a 64-bit fixed-point integer of
+                               the call's exponent e and added with integer
+                               atomics, so phi_grid and phi_grid_dde return
+                               the same bits on every run, alone or beside
+                               other work.  e makes every cell's sum below
+                               2^61 from the call's largest |W_i y_i| (times
+                               the DDE kernels' sums), the number of
+                               visibilities in the stack group and a bound
+                               on |[GC]|; each term is off by at most 2^-e/2
+                               (far below FP32 rounding, and below 1e-10 of
+                               the largest term times the visibility count
+                               in FP64).  Costs 16 bytes per resident grid
+                               cell (counted against max_grid_mib) and a
+                               conversion pass per group.  Not with
+                               grid_staging 1 (PHI_ERR_ARG).  No
+                               counterpart in the paper. */
   double oversample;        /* os; Npad = os * N must be an even integer     */
   double fov_rad;           /* full field of view in direction cosine        */
   double kmeans_tol;        /* Algorithm 1 convergence (default 1e-3)        */

@@ -52,7 +52,7 @@ class PlanDesc(ctypes.Structure):
         ("max_grid_mib", ctypes.c_int32),
         ("kernel_mode", ctypes.c_int32),
         ("grid_staging", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("grid_deterministic", ctypes.c_int32),
         ("oversample", ctypes.c_double),
         ("fov_rad", ctypes.c_double),
         ("kmeans_tol", ctypes.c_double),

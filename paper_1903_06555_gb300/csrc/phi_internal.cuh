@@ -17,7 +17,10 @@
 //   grids               padded complex grids of one group of stacks at a
 //                       time (as many as fit max_grid_mib), reused by every
 //                       group;
-//   counters            work-queue heads and quadrature statistics.
+//   counters            work-queue heads and quadrature statistics;
+//   fixed-point grids   grid_deterministic = 1 only: two int64 per cell of
+//                       the group's grids, the gridding sums before they
+//                       are rounded into the complex grids.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -109,6 +112,16 @@ struct RadialView {
   int buf;
 };
 
+// Deterministic gridding target (grid_deterministic = 1): per grid cell two
+// int64 (re, im) holding the cell's sum in units of 2^-exp[0], so that the
+// sum does not depend on the order of its additions; exp[1] != 0 marks a
+// non-finite visibility.  cells == nullptr: gridding adds its values to the
+// complex grid with FP atomics instead.
+struct FixedGrid {
+  unsigned long long* cells;
+  const int* exp;
+};
+
 // Kernel-side constants of one plan.
 struct QuadParams {
   double R;               // window radius (r units)
@@ -123,6 +136,7 @@ struct QuadParams {
   const void* node_hd;     // w_G(j) (FP32) or w_K(j) - w_G(j) (FP64), times 2 pi h g(r_j) r_j
   const uint16_t* tap_order;  // per even J_w: taps (a | b << 8) by distance from the box centre
   const int32_t* tap_off;     // offset of the list for J_w = 2 i + 2 at index i
+  FixedGrid fx;               // gridding target of deterministic plans
 };
 
 struct Plan {
@@ -192,6 +206,15 @@ struct Plan {
   void* radial_tab = nullptr;
   double radial_L = 0;
   int radial_buf = 0;
+  // deterministic gridding (grid_deterministic = 1): fixed-point sums of the
+  // group's grids (group * Npad^2 * 2 int64), the largest |W_i y_i| term
+  // factor of a call (double bits), the exponent and non-finite flag, and
+  // max over panel counts of sum_j |w_K(j) 2 pi h g(r_j) r_j|, which bounds
+  // every tap |[GC]| the quadrature can return
+  unsigned long long* fx_cells = nullptr;
+  unsigned long long* fx_max = nullptr;
+  int* fx_exp = nullptr;
+  double kernel_bound = 0;
 
   QuadParams quad() const {
     QuadParams q;
@@ -208,6 +231,8 @@ struct Plan {
     q.node_hd = node_hd;
     q.tap_order = tap_order;
     q.tap_off = tap_off;
+    q.fx.cells = fx_cells;
+    q.fx.exp = fx_exp;
     return q;
   }
 };
@@ -236,6 +261,7 @@ struct TableView {
   const void* pairs;   // C2<T> [(nw - 1) * nr]
   int64_t nr, nw;
   T inv_hr, inv_hw;
+  FixedGrid fx;        // gridding target of deterministic plans
 };
 
 // Stage timing (no-ops unless enabled): returns the start-event index or -1.
@@ -247,6 +273,7 @@ int launch_node_tables(Plan& p, cudaStream_t s);
 int launch_pixel_tables(Plan& p, cudaStream_t s);
 int build_kernel_table(Plan& p, cudaStream_t s);
 int build_radial_tables(Plan& p, cudaStream_t s);
+int compute_kernel_bound(Plan& p, double* scratch, cudaStream_t s);  // scratch: kMaxPanels doubles
 
 }  // namespace phi
 

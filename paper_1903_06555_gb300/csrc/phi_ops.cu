@@ -22,11 +22,14 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <mutex>
 #include <type_traits>
+#include <vector>
 
 #include "bessel_j0.cuh"
 #include "table_index.cuh"
+#include "fixed_point.cuh"
 #include "phi_internal.cuh"
 
 namespace phi {
@@ -171,6 +174,28 @@ __device__ __forceinline__ void atomic_add_c(float2* p, float2 v) { atomicAdd(p,
 __device__ __forceinline__ void atomic_add_c(double2* p, double2 v) {
   atomicAdd(&p->x, v.x);
   atomicAdd(&p->y, v.y);
+}
+
+// The fixed-point target shifted by `off` cells, as a grid pointer is.
+__device__ __forceinline__ FixedGrid fixed_offset(const FixedGrid& fx, int64_t off) {
+  FixedGrid r;
+  r.cells = fx.cells ? fx.cells + 2 * off : nullptr;
+  r.exp = fx.exp;
+  return r;
+}
+
+// Adds a gridding contribution to cell gi: to the complex grid with FP
+// atomics, or, for a deterministic plan, to the cell's fixed-point pair.
+template <typename C>
+__device__ __forceinline__ void grid_add(C* grid_out, const FixedGrid& fx, int64_t gi,
+                                         const C& add) {
+  if (fx.cells) {
+    const int e = __ldg(fx.exp);
+    atomicAdd(fx.cells + 2 * gi, static_cast<unsigned long long>(fixed_point(add.x, e)));
+    atomicAdd(fx.cells + 2 * gi + 1, static_cast<unsigned long long>(fixed_point(add.y, e)));
+  } else {
+    atomic_add_c(grid_out + gi, add);
+  }
 }
 
 // Circular grid index q mod n outside the loops: a division by a run-time n
@@ -356,6 +381,94 @@ __global__ void finish_kernel(const C* __restrict__ grids, const double* __restr
 }
 
 // ---------------------------------------------------------------------------
+// Deterministic gridding: fixed-point grid sums
+// ---------------------------------------------------------------------------
+
+// Per panel count P (thread P - 1): sum_j |w_K(j) 2 pi h g(r_j) r_j| over the
+// P-panel node table.  With |chirp| = 1 and |J0| <= 1 every quadrature value
+// of [GC] is bounded by it; the largest over P bounds them all.
+template <typename T>
+__global__ void kernel_bound_kernel(const T* __restrict__ hk, double* __restrict__ out) {
+  const int P = blockIdx.x * blockDim.x + threadIdx.x + 1;
+  if (P > kMaxPanels) return;
+  const int64_t off = panel_table_offset(P), n = static_cast<int64_t>(kNodes) * P;
+  double s = 0.0;
+  for (int64_t j = 0; j < n; ++j) s += fabs(static_cast<double>(hk[off + j]));
+  out[P - 1] = s;
+}
+
+// Largest term factor of one gridding call over records [0, n):
+// |W_i| (|Re y_i| + |Im y_i|), times (sum_s |a_i(s)|)(sum_s |b_i(s)|) with a
+// DDE, into *maxbits (the double's bits; non-negative doubles order as
+// unsigned integers).  Any non-finite factor stores +Inf.
+template <typename T, typename C>
+__global__ void fixed_bound_kernel(const VisRec<T>* __restrict__ recs,
+                                   const uint32_t* __restrict__ perm, int64_t n,
+                                   const C* __restrict__ vis, const C* __restrict__ dde_a,
+                                   const C* __restrict__ dde_b, int jd,
+                                   unsigned long long* maxbits) {
+  double m = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t src = perm[i] & 0x7fffffffu;
+    const C y = vis[src];
+    double f = fabs(static_cast<double>(recs[i].weight)) *
+               (fabs(static_cast<double>(y.x)) + fabs(static_cast<double>(y.y)));
+    if (dde_a) {
+      double sa = 0.0, sb = 0.0;
+      for (int j = 0; j < jd; ++j) {
+        const C a = dde_a[src * jd + j], b = dde_b[src * jd + j];
+        sa += fabs(static_cast<double>(a.x)) + fabs(static_cast<double>(a.y));
+        sb += fabs(static_cast<double>(b.x)) + fabs(static_cast<double>(b.y));
+      }
+      f *= sa * sb;
+    }
+    m = isfinite(f) ? fmax(m, f) : HUGE_VAL;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.0)
+    atomicMax(maxbits, static_cast<unsigned long long>(__double_as_longlong(m)));
+}
+
+// The exponent e of a call: every partial sum of a cell is at most
+// n_terms * bound * max factor, and e keeps that below 2^61 (clamped to
+// [-90, 120]); exp[1] = 1 for a non-finite factor.
+__global__ void fixed_exp_kernel(const unsigned long long* __restrict__ maxbits, double scale,
+                                 int* __restrict__ exp) {
+  const double A = __longlong_as_double(static_cast<long long>(*maxbits)) * scale;
+  if (!isfinite(A)) {
+    exp[0] = 0;
+    exp[1] = 1;
+    return;
+  }
+  int ex = 0;
+  if (A > 0.0) frexp(A, &ex);   // A < 2^ex
+  exp[0] = min(max(61 - ex, -90), 120);
+  exp[1] = 0;
+}
+
+// The fixed-point sums rounded into the complex grids (from_fixed), NaN
+// throughout after a non-finite visibility.
+template <typename T, typename C>
+__global__ void fixed_to_grid_kernel(const longlong2* __restrict__ cells,
+                                     const int* __restrict__ exp, int64_t n,
+                                     C* __restrict__ grid) {
+  const int e = exp[0];
+  const bool bad = exp[1] != 0;
+  const T s_hi = static_cast<T>(ldexp(1.0, 32 - e)), s_lo = static_cast<T>(ldexp(1.0, -e));
+  const T nan = static_cast<T>(NAN);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const longlong2 v = cells[i];
+    C out;
+    out.x = bad ? nan : from_fixed(v.x, s_hi, s_lo);
+    out.y = bad ? nan : from_fixed(v.y, s_hi, s_lo);
+    grid[i] = out;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Fused kernel quadrature
 // ---------------------------------------------------------------------------
 
@@ -489,7 +602,7 @@ __device__ __forceinline__ void panel_pair(float2 x, float4 v, float2 g, const f
                                            float2 (&KI)[NT], float (&gr)[NT], float (&gi)[NT]) {
 #pragma unroll
   for (int t = 0; t < NT; ++t) {
-    const float2 u = make_float2(fmaf(x.x, Bh[t], a[t]), fmaf(x.y, Bh[t], a[t]));
+    const float2 u = __ffma2_rn(x, make_float2(Bh[t], Bh[t]), make_float2(a[t], a[t]));
     const float2 J = j0_pair_regime<R>(u);
     KR[t] = __ffma2_rn(J, make_float2(v.x, v.y), KR[t]);
     KI[t] = __ffma2_rn(J, make_float2(v.z, v.w), KI[t]);
@@ -796,12 +909,13 @@ __device__ __forceinline__ C load_visibility(const C* __restrict__ vis_in, uint3
 // K times the cell.
 template <typename C, bool kGrid>
 __device__ __forceinline__ void apply_tap(const C& K, int64_t gi, const C& yv,
-                                          const C* __restrict__ grid_in, C* grid_out, C& accv) {
+                                          const C* __restrict__ grid_in, C* grid_out,
+                                          const FixedGrid& fx, C& accv) {
   if (kGrid) {
     C add;
     add.x = K.x * yv.x + K.y * yv.y;   // conj(K) * yv
     add.y = K.x * yv.y - K.y * yv.x;
-    atomic_add_c(grid_out + gi, add);
+    grid_add(grid_out, fx, gi, add);
   } else {
     const C g = grid_in[gi];
     accv.x += K.x * g.x - K.y * g.y;
@@ -926,7 +1040,7 @@ __global__ void __launch_bounds__(VisLaunch<T>::threads, VisLaunch<T>::min_block
           const int ov = static_cast<int>(code[k] >> 8) - half + 1;
           const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                              wrap_index(r.bu + ou, npad);
-          apply_tap<C, kGrid>(K[k], gi, yv, grid_in, grid_out, accv);
+          apply_tap<C, kGrid>(K[k], gi, yv, grid_in, grid_out, q.fx, accv);
         }
     }
     if (lane == 0) my_taps += static_cast<unsigned long long>(ntap);
@@ -1027,8 +1141,8 @@ template <bool kContig, bool kGrid, typename T, typename C>
 __device__ __forceinline__ void table_vis_taps(const KPair<C>* __restrict__ row,
                                                const VisRec<T>& r, T fw, int nr, T inv_hr,
                                                int npad, const C* __restrict__ grid_in,
-                                               C* grid_out, C yv, C ys, C& sx, C& sy,
-                                               int lane) {
+                                               C* grid_out, const FixedGrid& fx, C yv, C ys,
+                                               C& sx, C& sy, int lane) {
   const int Jw = r.jw, half = Jw / 2, ntap = Jw * Jw;
   const T last_r = static_cast<T>(nr - 2);
   int a = lane % Jw, b = lane / Jw;
@@ -1056,7 +1170,7 @@ __device__ __forceinline__ void table_vis_taps(const KPair<C>* __restrict__ row,
         C add;
         add.x = fma(K.x, yv.x, K.y * ys.x);
         add.y = fma(K.x, yv.y, K.y * ys.y);
-        atomic_add_c(grid_out + gi, add);
+        grid_add(grid_out, fx, gi, add);
       } else {
         const C g = grid_in[gi];
         sx.x = fma(K.x, g.x, sx.x);
@@ -1086,8 +1200,8 @@ __device__ __forceinline__ void table_vis_taps(const KPair<C>* __restrict__ row,
 template <bool kGrid, typename T, typename C>
 __device__ __forceinline__ C table_vis(const KPair<C>* __restrict__ row, const VisRec<T>& r,
                                        T fw, int nr, T inv_hr, int npad,
-                                       const C* __restrict__ grid_in, C* grid_out, C yv,
-                                       int lane) {
+                                       const C* __restrict__ grid_in, C* grid_out,
+                                       const FixedGrid& fx, C yv, int lane) {
   const int Jw = r.jw, half = Jw / 2;
   const T sg = r.dw < 0.0 ? T(-1) : T(1);
   C ys;
@@ -1098,10 +1212,11 @@ __device__ __forceinline__ C table_vis(const KPair<C>* __restrict__ row, const V
   if (u0 + Jw <= npad && v0 + Jw <= npad) {
     const int64_t o0 = static_cast<int64_t>(v0) * npad + u0;
     table_vis_taps<true, kGrid>(row, r, fw, nr, inv_hr, npad, kGrid ? nullptr : grid_in + o0,
-                                kGrid ? grid_out + o0 : nullptr, yv, ys, sx, sy, lane);
+                                kGrid ? grid_out + o0 : nullptr, fixed_offset(fx, o0), yv, ys,
+                                sx, sy, lane);
   } else {
-    table_vis_taps<false, kGrid>(row, r, fw, nr, inv_hr, npad, grid_in, grid_out, yv, ys, sx,
-                                 sy, lane);
+    table_vis_taps<false, kGrid>(row, r, fw, nr, inv_hr, npad, grid_in, grid_out, fx, yv, ys,
+                                 sx, sy, lane);
   }
   C acc;   // sum of (Kx + i s Ky) g
   acc.x = fma(-sg, sy.y, sx.x);
@@ -1143,7 +1258,8 @@ __global__ void __launch_bounds__(256) vis_table_kernel(const VisRec<T>* __restr
                        : cmake<C>(0.0, 0.0);
     const C accv = table_vis<kGrid>(pairs + static_cast<int64_t>(jrow) * nr, r, fw, nr,
                                     tv.inv_hr, npad, kGrid ? nullptr : grid_in + gbase,
-                                    kGrid ? grid_out + gbase : nullptr, yv, lane);
+                                    kGrid ? grid_out + gbase : nullptr,
+                                    fixed_offset(tv.fx, gbase), yv, lane);
     if (lane == 0) my_taps += static_cast<unsigned long long>(r.jw * r.jw);
     if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
   }
@@ -1314,7 +1430,8 @@ __global__ void __launch_bounds__(256) row_table_kernel(
                          : cmake<C>(0.0, 0.0);
       const C accv = table_vis<kGrid>(row, r, fw, nr, tv.inv_hr, npad,
                                       kGrid ? nullptr : grid_in + gbase,
-                                      kGrid ? grid_out + gbase : nullptr, yv, lane);
+                                      kGrid ? grid_out + gbase : nullptr,
+                                      fixed_offset(tv.fx, gbase), yv, lane);
       if (lane == 0) my_taps += static_cast<unsigned long long>(r.jw * r.jw);
       if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
     }
@@ -1528,7 +1645,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
         const C K = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
-        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, accv);
+        apply_tap<C, kGrid>(K, gi, yv, grid_in, grid_out, q.fx, accv);
       }
       a += step_a;
       b += step_b;
@@ -1655,7 +1772,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
         const int ou = cu - h - half + 1, ov = cv - h - half + 1;
         const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
                            wrap_index(r.bu + ou, npad);
-        apply_tap<C, kGrid>(acc, gi, yv, grid_in, grid_out, accv);
+        apply_tap<C, kGrid>(acc, gi, yv, grid_in, grid_out, q.fx, accv);
       }
     }
     // the box and the DDE taps are rewritten for the next visibility
@@ -1762,6 +1879,8 @@ TableView<T> table_view(const Plan& p) {
   v.nw = p.table_nw;
   v.inv_hr = static_cast<T>(1.0 / p.table_hr);
   v.inv_hw = static_cast<T>(1.0 / p.table_hw);
+  v.fx.cells = p.fx_cells;
+  v.fx.exp = p.fx_exp;
   return v;
 }
 
@@ -2007,19 +2126,59 @@ int run_degrid(Plan& p, const T* x, C* y, cudaStream_t s, const DdeArgs* dde = n
   return PHI_OK;
 }
 
+// Deterministic plans, before a group's gridding: zero its fixed-point sums
+// and set the exponent e from the call's largest term.  A cell receives at
+// most one term per visibility and period of the grid its box covers, each
+// at most |[GC]| times the visibility's factor; the bound on |[GC]| carries
+// a factor 4 for the radial mode's Chebyshev interpolation (its Lebesgue
+// constant is below 3 at 16 and 24 points) and the FP32 J0's rounding.
+template <typename T, typename C>
+int fixed_prepare(Plan& p, int g, const C* y, const DdeArgs* dde, cudaStream_t s) {
+  const int64_t plane = static_cast<int64_t>(p.npad) * p.npad;
+  const int n = static_cast<int>(p.group_off[g + 1] - p.group_off[g]);
+  PHI_CUDA_TRY(cudaMemsetAsync(p.fx_cells, 0, 2 * sizeof(long long) * plane * n, s));
+  PHI_CUDA_TRY(cudaMemsetAsync(p.fx_max, 0, sizeof(unsigned long long), s));
+  const int64_t b0 = p.stack_off[p.group_stacks[p.group_off[g]]];
+  const int64_t nk = p.stack_off[p.group_stacks[p.group_off[g + 1] - 1] + 1] - b0;
+  if (nk > 0) {
+    const int blocks = static_cast<int>(std::min<int64_t>(p.num_sms * 4, (nk + 255) / 256));
+    fixed_bound_kernel<T, C><<<blocks, 256, 0, s>>>(
+        static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, y,
+        dde ? static_cast<const C*>(dde->a) : nullptr,
+        dde ? static_cast<const C*>(dde->b) : nullptr, dde ? dde->jd : 0, p.fx_max);
+    PHI_CUDA_TRY(cudaGetLastError());
+  }
+  const int jbox = std::max(p.max_jw, 2) + (dde ? dde->jd - 1 : 0);
+  const double periods = std::ceil(static_cast<double>(jbox) / p.npad);
+  const double scale = 4.0 * p.kernel_bound * static_cast<double>(std::max<int64_t>(nk, 1)) *
+                       periods * periods;
+  fixed_exp_kernel<<<1, 1, 0, s>>>(p.fx_max, scale, p.fx_exp);
+  PHI_CUDA_TRY(cudaGetLastError());
+  return PHI_OK;
+}
+
 template <typename T, typename C>
 int run_grid(Plan& p, const C* y, T* x, cudaStream_t s, const DdeArgs* dde = nullptr) {
   PHI_CUDA_TRY(cudaMemsetAsync(p.counters, 0, sizeof(unsigned long long) * p.K, s));
   C* grids = static_cast<C*>(p.grid);
   const int64_t plane = static_cast<int64_t>(p.npad) * p.npad;
   const int ngroups = static_cast<int>(p.group_off.size()) - 1;
+  const bool fixed = p.fx_cells != nullptr;
   for (int g = 0; g < ngroups; ++g) {
     const int n = static_cast<int>(p.group_off[g + 1] - p.group_off[g]);
     long ev = timer_begin(p, s);
-    PHI_CUDA_TRY(cudaMemsetAsync(grids, 0, sizeof(C) * plane * n, s));
+    if (fixed)
+      PHI_TRY_ST((fixed_prepare<T, C>(p, g, y, dde, s)));
+    else
+      PHI_CUDA_TRY(cudaMemsetAsync(grids, 0, sizeof(C) * plane * n, s));
     timer_end(p, ev, PHI_STAGE_CLEAR, s);
     ev = timer_begin(p, s);
     PHI_TRY_ST((launch_group_kernel<T, C, true>(p, g, nullptr, grids, y, nullptr, s, dde)));
+    if (fixed) {
+      fixed_to_grid_kernel<T, C><<<p.num_sms * 8, 256, 0, s>>>(
+          reinterpret_cast<const longlong2*>(p.fx_cells), p.fx_exp, plane * n, grids);
+      PHI_CUDA_TRY(cudaGetLastError());
+    }
     timer_end(p, ev, PHI_STAGE_GRID, s);
     ev = timer_begin(p, s);
     PHI_TRY_ST((fft_group<T, C>(p, grids, n, CUFFT_INVERSE, s)));
@@ -2066,6 +2225,23 @@ int build_kernel_table(Plan& p, cudaStream_t s) {
 int build_radial_tables(Plan& p, cudaStream_t s) {
   if (p.d.precision == PHI_F64) return build_radial_tables_t<double, double2>(p, s);
   return build_radial_tables_t<float, float2>(p, s);
+}
+
+int compute_kernel_bound(Plan& p, double* scratch, cudaStream_t s) {
+  const int blocks = (kMaxPanels + 127) / 128;
+  if (p.d.precision == PHI_F64)
+    kernel_bound_kernel<double><<<blocks, 128, 0, s>>>(static_cast<const double*>(p.node_hk),
+                                                       scratch);
+  else
+    kernel_bound_kernel<float><<<blocks, 128, 0, s>>>(static_cast<const float*>(p.node_hk),
+                                                      scratch);
+  PHI_CUDA_TRY(cudaGetLastError());
+  std::vector<double> h(kMaxPanels);
+  PHI_CUDA_TRY(cudaMemcpyAsync(h.data(), scratch, sizeof(double) * kMaxPanels,
+                               cudaMemcpyDeviceToHost, s));
+  PHI_CUDA_TRY(cudaStreamSynchronize(s));
+  p.kernel_bound = *std::max_element(h.begin(), h.end());
+  return PHI_OK;
 }
 
 long timer_begin(Plan& p, cudaStream_t s) {

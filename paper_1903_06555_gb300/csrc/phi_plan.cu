@@ -340,6 +340,9 @@ void free_plan(Plan* p) {
   cudaFree(p->group_stacks_dev);
   cudaFree(p->stack_slot_dev);
   cudaFree(p->wbar_dev);
+  cudaFree(p->fx_cells);
+  cudaFree(p->fx_max);
+  cudaFree(p->fx_exp);
   if (p->fft_batch_ok) cufftDestroy(p->fft_batch);
 }
 
@@ -383,7 +386,10 @@ int validate(const phi_plan_desc& d, int64_t M) {
       d.kernel_mode != PHI_KERNEL_RADIAL)
     return PHI_ERR_ARG;
   if (d.grid_staging < 0 || d.grid_staging > 2) return PHI_ERR_ARG;
-  if (d.max_grid_mib < 0 || d.reserved0 != 0) return PHI_ERR_ARG;
+  if (d.max_grid_mib < 0) return PHI_ERR_ARG;
+  if (d.grid_deterministic != 0 && d.grid_deterministic != 1) return PHI_ERR_ARG;
+  // uv-tile staging sums in shared memory with FP atomics first
+  if (d.grid_deterministic && d.grid_staging == 1) return PHI_ERR_ARG;
   if (d.grid_staging && d.kernel_mode != PHI_KERNEL_TABLE) return PHI_ERR_ARG;
   if (d.kernel_mode == PHI_KERNEL_TABLE && !(d.table_tol > 0.0 && d.table_tol < 1.0))
     return PHI_ERR_ARG;
@@ -651,6 +657,27 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
       return PHI_ERR_ARG;
   }
 
+  // --- stack groups: the stacks with visibilities, `group` at a time, their
+  // grids resident together (as many as fit max_grid_mib, at least one)
+  const size_t grid_bytes = 2 * (f64 ? sizeof(double) : sizeof(float)) *
+                            static_cast<size_t>(p.npad) * p.npad;
+  // a deterministic plan also holds two int64 per cell of every resident grid
+  const size_t fx_bytes =
+      d.grid_deterministic ? 2 * sizeof(long long) * static_cast<size_t>(p.npad) * p.npad : 0;
+  p.group_stacks.clear();
+  for (int q = 0; q < K; ++q)
+    if (p.stack_off[q + 1] > p.stack_off[q]) p.group_stacks.push_back(q);
+  const double budget = (d.max_grid_mib > 0 ? d.max_grid_mib : 4096) * 1048576.0;
+  p.group = static_cast<int>(std::max<double>(1.0, std::floor(budget / (grid_bytes + fx_bytes))));
+  p.group = std::max(1, std::min<int>(p.group, static_cast<int>(p.group_stacks.size())));
+  p.group_off.assign(1, 0);
+  for (size_t g = 0; g < p.group_stacks.size(); g += p.group)
+    p.group_off.push_back(static_cast<int64_t>(std::min(p.group_stacks.size(), g + p.group)));
+  std::vector<int32_t> slot(K, 0);
+  for (size_t g = 0; g + 1 < p.group_off.size(); ++g)
+    for (int64_t i = p.group_off[g]; i < p.group_off[g + 1]; ++i)
+      slot[p.group_stacks[i]] = static_cast<int32_t>(i - p.group_off[g]);
+
   // --- work items of the table path's staged kernels: runs of equal key in
   // the sorted kept records (grid_staging 1: uv tiles, in record order;
   // grid_staging 2: w-rows, through the index p.row_idx), split into items of
@@ -749,22 +776,6 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   PHI_CUDA_TRY(owned_alloc(p, &p.omn_pix, static_cast<size_t>(p.N) * p.N));
   PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.corr_pix),
                            tsize * p.N * static_cast<size_t>(p.N)));
-  // Stack groups: the stacks with visibilities, `group` at a time, their
-  // grids resident together (as many as fit max_grid_mib, at least one).
-  const size_t grid_bytes = 2 * tsize * static_cast<size_t>(p.npad) * p.npad;
-  p.group_stacks.clear();
-  for (int q = 0; q < K; ++q)
-    if (p.stack_off[q + 1] > p.stack_off[q]) p.group_stacks.push_back(q);
-  const double budget = (d.max_grid_mib > 0 ? d.max_grid_mib : 4096) * 1048576.0;
-  p.group = static_cast<int>(std::max<double>(1.0, std::floor(budget / grid_bytes)));
-  p.group = std::max(1, std::min<int>(p.group, static_cast<int>(p.group_stacks.size())));
-  p.group_off.assign(1, 0);
-  for (size_t g = 0; g < p.group_stacks.size(); g += p.group)
-    p.group_off.push_back(static_cast<int64_t>(std::min(p.group_stacks.size(), g + p.group)));
-  std::vector<int32_t> slot(K, 0);
-  for (size_t g = 0; g + 1 < p.group_off.size(); ++g)
-    for (int64_t i = p.group_off[g]; i < p.group_off[g + 1]; ++i)
-      slot[p.group_stacks[i]] = static_cast<int32_t>(i - p.group_off[g]);
   PHI_CUDA_TRY(owned_alloc(p, &p.group_stacks_dev, std::max<size_t>(1, p.group_stacks.size())));
   PHI_CUDA_TRY(owned_alloc(p, &p.stack_slot_dev, K));
   PHI_CUDA_TRY(owned_alloc(p, &p.wbar_dev, K));
@@ -777,6 +788,14 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
                            grid_bytes * static_cast<size_t>(p.group)));
   PHI_TRY(launch_node_tables(p, s));
   PHI_TRY(launch_pixel_tables(p, s));
+  if (d.grid_deterministic) {
+    PHI_CUDA_TRY(owned_alloc(p, &p.fx_cells, 2 * static_cast<size_t>(p.npad) * p.npad * p.group));
+    PHI_CUDA_TRY(owned_alloc(p, &p.fx_max, 1));
+    PHI_CUDA_TRY(owned_alloc(p, &p.fx_exp, 2));
+    double* bound = nullptr;
+    PHI_CUDA_TRY(tmp.alloc(&bound, kMaxPanels));
+    PHI_TRY(compute_kernel_bound(p, bound, s));
+  }
   if (d.kernel_mode == PHI_KERNEL_TABLE) {
     const size_t pair = 2 * 2 * tsize;
     PHI_CUDA_TRY(owned_alloc(p, reinterpret_cast<unsigned char**>(&p.table),

@@ -84,8 +84,10 @@ def estimate_bytes(req: Request, planned: bool = False) -> int:
     sort keys and values with their CUB buffers), the records, per-pixel
     tables, the padded grids of one stack group (as many stacks as fit
     max_grid_mib, default 4 GiB) and cuFFT workspace (at most one grid per
-    batched transform plus one).  A request that may raise its stacks is
-    charged for the most stacks a retry can reach (126)."""
+    batched transform plus one), and with grid_deterministic the
+    fixed-point sums of the group's grids (16 bytes a cell).  A request that
+    may raise its stacks is charged for the most stacks a retry can reach
+    (126)."""
     m = int(req.uvw.shape[0])
     n = int(req.desc["image_n"])
     os_ = float(req.desc.get("oversample", 2.0))
@@ -100,10 +102,12 @@ def estimate_bytes(req: Request, planned: bool = False) -> int:
     per_vis = 24 + 8 + 1 + 4 + 16 + 16 + (52 if f64 else 36)
     per_pix = 12 + r
     grid = c * npad * npad
+    fixed = 16 * npad * npad if int(req.desc.get("grid_deterministic", 0)) else 0
     k = 126 if req.raise_stacks else int(req.desc.get("n_stacks", 1))
     cap = (int(req.desc.get("max_grid_mib", 0)) or 4096) << 20
-    group = max(1, min(k, cap // grid))
-    return io + m * per_vis + n * n * per_pix + (2 * group + 1) * grid + (8 << 20)
+    group = max(1, min(k, cap // (grid + fixed)))
+    return (io + m * per_vis + n * n * per_pix + (2 * group + 1) * grid + group * fixed +
+            (8 << 20))
 
 
 class Server:

@@ -55,7 +55,7 @@ int main(void) {
   O(phi_plan_summary, image_n); O(phi_plan_summary, du); O(phi_plan_summary, support_coeff);
   O(phi_plan_summary, kernel_mode); O(phi_plan_summary, table_n_rho); O(phi_plan_summary, table_h_w);
   O(phi_plan_desc, kernel_mode); O(phi_plan_desc, table_tol); O(phi_plan_desc, max_grid_mib);
-  O(phi_plan_desc, reserved0); O(phi_plan_summary, group);
+  O(phi_plan_desc, grid_deterministic); O(phi_plan_summary, group);
   printf("phi_wkernel_params %zu\n", sizeof(phi_wkernel_params));
   O(phi_wkernel_params, cycles_per_panel); O(phi_wkernel_params, precision);
   return 0;
@@ -103,7 +103,8 @@ BAD = [dict(image_n=127), dict(image_n=0), dict(support=3), dict(n_stacks=0),
        dict(max_support=2), dict(quad_rel_tol=0.0), dict(support_rule=3), dict(max_refine=-1),
        dict(kernel_mode=3), dict(kernel_mode=1, table_tol=0.0), dict(grid_staging=2),
        dict(kernel_mode=2, grid_staging=1),
-       dict(grid_staging=1), dict(max_grid_mib=-1), dict(reserved0=1)]
+       dict(grid_staging=1), dict(max_grid_mib=-1), dict(grid_deterministic=2),
+       dict(grid_deterministic=1, kernel_mode=1, grid_staging=1)]
 
 
 @pytest.mark.parametrize("bad", BAD)

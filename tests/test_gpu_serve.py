@@ -1,7 +1,8 @@
 """Serving: continuous batching with HBM-budget admission, overlapping
 requests, resident plans, failure isolation; every result equals the same
 request run alone, within the stated tolerance (degrid 1e-6, grid 1e-5
-relative: gridding accumulates with float atomics, whose order varies)."""
+relative: gridding accumulates with float atomics, whose order varies), and
+bit for bit with deterministic gridding."""
 import math
 
 import numpy as np
@@ -56,6 +57,24 @@ def test_results_alone_equal_results_in_the_mix():
             assert np.linalg.norm(got.dirty - ref.dirty) <= 1e-5 * den
     summary = S.summarize(mixed)
     assert summary["ok"] == len(reqs) and summary["latency_p99_s"] >= summary["latency_p50_s"]
+
+
+def test_deterministic_plans_give_the_same_bits_alone_and_in_the_mix():
+    """With grid_deterministic = 1 gridding no longer depends on the order of
+    its additions, so a request's dirty image, like its visibilities, is
+    bit for bit the one it gets alone, whatever else runs beside it."""
+    reqs = make_requests(seed=2, n=6)
+    for r in reqs:
+        r.desc = dict(r.desc, grid_deterministic=1)
+        r.ops = ("degrid", "grid")
+    budget = 3 * max(S.estimate_bytes(r) for r in reqs)
+    with S.Server(hbm_budget_bytes=budget, slots=4) as srv:
+        mixed = srv.run_stream(reqs)
+    assert all(r.status == "ok" for r in mixed)
+    for req, got in zip(reqs, mixed):
+        ref = run_alone(req)
+        assert np.array_equal(got.y, ref.y)
+        assert np.array_equal(got.dirty, ref.dirty)
 
 
 def test_failures_are_isolated_and_plans_stay_resident():

@@ -50,3 +50,21 @@ def test_padded_grid_size_rounds_halves_up_like_the_library():
     base = S.estimate_bytes(req(77, 1, oversample=2.5 - 1e-9))   # 192.49... -> 192
     # one stack: its grid, one batched-transform workspace grid, one more
     assert S.estimate_bytes(r) - base == 3 * (grid_193 - grid_192)
+
+
+def test_deterministic_plans_are_charged_for_their_fixed_point_grids():
+    """grid_deterministic adds two int64 per cell of each resident grid and
+    counts them against max_grid_mib when sizing the stack group."""
+    grid = 8 * 1024 * 1024                      # 512^2 image, 1024^2 complex64 grid
+    fixed = 16 * 1024 * 1024
+    assert (S.estimate_bytes(req(512, 8, grid_deterministic=1)) -
+            S.estimate_bytes(req(512, 8)) == 8 * fixed)
+    # 8192^2 image: a 2 GiB grid and 4 GiB of sums per stack exceed the 4 GiB
+    # default, so one stack per group: 3 grids + 1 set of sums, against
+    # 5 grids for the plain plan's groups of 2
+    big = 8 * 16384 * 16384
+    e_plain = S.estimate_bytes(req(8192, 64))
+    e_det = S.estimate_bytes(req(8192, 64, grid_deterministic=1))
+    assert e_det - e_plain == (3 * big + 2 * big) - 5 * big
+    assert (S.estimate_bytes(req(8192, 1, grid_deterministic=1)) -
+            S.estimate_bytes(req(8192, 1)) == 2 * big)
