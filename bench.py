@@ -1127,9 +1127,13 @@ def run_dde(args):
               "rel_l2_vs_quadrature_box": float(torch.linalg.vector_norm(yr - yq) /
                                                 torch.linalg.vector_norm(yq))}
     rplan.close()
-    # executed work: the quadrature tap-nodes of the w-kernel boxes and, per
-    # combined tap, (J_D^2 + J_D) complex multiply-adds of 8 flops
-    flops = (nodes * FLOPS_PER_TAP_NODE + taps * (jd * jd + jd) * 8.0) / calls
+    # executed work: the quadrature tap-nodes of the w-kernel boxes and the
+    # separable convolution's complex multiply-adds (8 flops each): per
+    # visibility of support J_w, J_D J_w^2 for the row pass (J_w rows of the
+    # J_w + J_D - 1 columns, J_D taps inside the box per w-kernel tap) and
+    # J_D J_w (J_w + J_D - 1) for the column pass
+    macs = sum(c * jd * j * (j + j + jd - 1) for c, j in zip(info["counts"], info["jw"]))
+    flops = nodes * FLOPS_PER_TAP_NODE / calls + macs * 8.0
     ach = flops / (ms_dde / 2 / 1e3) / 1e12
     peaks = measured_peaks()
     peak_fp32 = fp32_peak_tflops(device_sms(), peaks.get("sm_max_mhz", 2070.0))
@@ -1145,7 +1149,8 @@ def run_dde(args):
             "roofline": {"bound": "alu", "kernel": "vis_dde_kernel", "achieved": ach,
                          "peak": peak_fp32, "unit": "TFLOP/s", "frac": ach / peak_fp32,
                          "work_note": "executed work: 36 flops per quadrature tap-node + "
-                                      "(J_D^2 + J_D) complex multiply-adds per combined tap"}}
+                                      "J_D J_w (2 J_w + J_D - 1) complex multiply-adds per "
+                                      "visibility (separable row and column passes)"}}
     print(json.dumps(line), flush=True)
 
 

@@ -1677,7 +1677,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
 // mode's series -- then forms every tap of the (J_w + J_D - 1)^2 box as
 // C(q) = sum_s D(s) [GC](u - q - s), i.e. from the stored taps K[q + s - q0].
 template <typename T, typename C, bool kGrid, bool kRadial>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) vis_dde_kernel(
     const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
     const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
     C* __restrict__ vis_out, QuadParams q, RadialView<T> rv, const C* __restrict__ dde_a,
@@ -1691,6 +1691,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
            warp * (box_max * box_max + 2 * jd + (kRadial ? rv.buf : 0));
   C* dab = box + box_max * box_max;   // a_i then b_i
   C* ser = dab + 2 * jd;              // kRadial: the visibility's series
+  // jd rows x 32 lanes of the row pass, in the node buffer (free once the
+  // box is complete; the next visibility rebuilds its nodes anyway)
+  C* ring = reinterpret_cast<C*>(sh);
+  static_assert(32 * 15 * sizeof(C) <= kNodeBatch * sizeof(NodeVal<T>),
+                "the row-pass ring of the largest DDE kernel must fit the node buffer");
   const int h = jd >> 1;
   unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
   const int npad = q.npad;
@@ -1723,50 +1728,90 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_dde_kernel(
         box[t] = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
       }
     } else {
-    // 1. the w-kernel on the J_w box, by the per-tap quadrature (ring order)
-    for (int t0 = 0; t0 < ntap; t0 += 32) {
-      const int t = t0 + lane;
-      const bool active = t < ntap;
-      const uint32_t code = order[active ? t : 0];
-      const int ka = static_cast<int>(code & 0xffu), kb = static_cast<int>(code >> 8);
-      const T du_ = fu - static_cast<T>(ka - half + 1), dv_ = fv - static_cast<T>(kb - half + 1);
-      const T rho = sqrt(du_ * du_ + dv_ * dv_);
-      T rmax = active ? rho : T(0);
+      // 1. the w-kernel on the J_w box, by the per-tap quadrature: ring
+      // order, kVisTaps taps per lane, as in vis_kernel
+      for (int t0 = 0; t0 < ntap; t0 += 32 * kVisTaps) {
+        T rho[kVisTaps];
+        bool act[kVisTaps], ok[kVisTaps];
+        uint32_t code[kVisTaps];
+        T rmax = T(0);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-      const int npan = initial_panels(q, static_cast<float>(rmax), adw);
-      bool ok = true;
-      const C K = eval_chunk<T, C>(sh, q, rho, active, r.dw, npan, kMaxPanels, built, ok, lane, my_nodes);
-      if (active) {
-        box[kb * Jw + ka] = K;
-        if (!ok) ++my_bad;
+        for (int k = 0; k < kVisTaps; ++k) {
+          const int t = t0 + 32 * k + lane;
+          act[k] = t < ntap;
+          code[k] = order[act[k] ? t : 0];
+          const T du_ = fu - static_cast<T>(static_cast<int>(code[k] & 0xffu) - half + 1);
+          const T dv_ = fv - static_cast<T>(static_cast<int>(code[k] >> 8) - half + 1);
+          rho[k] = sqrt(du_ * du_ + dv_ * dv_);
+          if (act[k]) rmax = fmax(rmax, rho[k]);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        const int npan = initial_panels(q, static_cast<float>(rmax), adw);
+        C K[kVisTaps];
+        eval_chunk_nt<kVisTaps>(sh, q, rho, act, r.dw, npan, kMaxPanels, built, ok, lane,
+                                my_nodes, K);
+#pragma unroll
+        for (int k = 0; k < kVisTaps; ++k)
+          if (act[k]) {
+            box[(code[k] >> 8) * Jw + (code[k] & 0xffu)] = K[k];
+            if (!ok[k]) ++my_bad;
+          }
       }
     }
-    }
     __syncwarp();
-    // 2. the combined taps, raster order over the J_w + 2 h box
+    // 2. the combined taps over the (J_w + 2 h)^2 box, by separability:
+    // C(cv, cu) = sum_sv b(sv) R(cv - h + sv, cu) with the row pass
+    // R(kb, cu) = sum_su a(su) K(kb, cu - h + su).  Each lane takes one
+    // column cu and a run of rows [r0, r1), walking down it: row kb of R is
+    // formed once, when the walk reaches it (the 2 h rows above r0 first),
+    // into slot kb mod jd of the lane's own ring column, and stays there
+    // while rows kb .. kb + 2 h read it.  Columns go 32 at a time; a block of
+    // nb < 32 columns splits its rows into 32 / nb runs so that the lanes
+    // stay busy.
     C accv = cmake<C>(0.0, 0.0);
-    const int Jc = Jw + 2 * h, nc = Jc * Jc;
-    for (int c0 = 0; c0 < nc; c0 += 32) {
-      const int c = c0 + lane;
-      if (c < nc) {
-        const int cv = c / Jc, cu = c - cv * Jc;
+    const int Jc = Jw + 2 * h;
+    for (int c0 = 0; c0 < Jc; c0 += 32) {
+      const int nb = min(32, Jc - c0);
+      const int runs = 32 / nb, len = (Jc + runs - 1) / runs;
+      const int run = lane / nb, cu = c0 + lane - run * nb;
+      const int r0 = run * len, r1 = min(Jc, r0 + len);
+      if (run >= runs || r0 >= r1) continue;
+      C* ring_l = ring + lane;
+      // row kb of R at column cu into its slot
+      auto row_pass = [&](int kb, int slot) {
+        C rv_ = cmake<C>(0.0, 0.0);
+        const C* krow = box + kb * Jw;
+        for (int s = 0; s < jd; ++s) {
+          const int ka = cu - 2 * h + s;
+          if (ka < 0 || ka >= Jw) continue;
+          const C kv = krow[ka];
+          const C av = dab[s];
+          rv_.x += av.x * kv.x - av.y * kv.y;
+          rv_.y += av.x * kv.y + av.y * kv.x;
+        }
+        ring_l[slot * 32] = rv_;
+      };
+      int slot = max(0, r0 - 2 * h) % jd;
+      for (int kb = max(0, r0 - 2 * h); kb < min(r0, Jw); ++kb) {
+        row_pass(kb, slot);
+        slot = slot + 1 == jd ? 0 : slot + 1;
+      }
+      for (int cv = r0; cv < r1; ++cv) {
+        if (cv < Jw) {
+          row_pass(cv, slot);
+          slot = slot + 1 == jd ? 0 : slot + 1;
+        }
+        // rows kb = cv - 2 h .. cv of R (b index kb - cv + 2 h), those in the box
+        const int lo = max(0, cv - 2 * h), hi = min(Jw - 1, cv);
         C acc = cmake<C>(0.0, 0.0);
-        for (int sv = -h; sv <= h; ++sv) {
-          const int kb = cv - h + sv;
-          if (kb < 0 || kb >= Jw) continue;
-          C row = cmake<C>(0.0, 0.0);
-          for (int su = -h; su <= h; ++su) {
-            const int ka = cu - h + su;
-            if (ka < 0 || ka >= Jw) continue;
-            const C kv = box[kb * Jw + ka];
-            const C av = dab[su + h];
-            row.x += av.x * kv.x - av.y * kv.y;
-            row.y += av.x * kv.y + av.y * kv.x;
-          }
-          const C bv = dab[jd + sv + h];
-          acc.x += bv.x * row.x - bv.y * row.y;
-          acc.y += bv.x * row.y + bv.y * row.x;
+        int sl = lo % jd;
+        for (int kb = lo; kb <= hi; ++kb) {
+          const C rv2 = ring_l[sl * 32];
+          const C bv = dab[jd + kb - cv + 2 * h];
+          acc.x += bv.x * rv2.x - bv.y * rv2.y;
+          acc.y += bv.x * rv2.y + bv.y * rv2.x;
+          sl = sl + 1 == jd ? 0 : sl + 1;
         }
         ++my_taps;
         const int ou = cu - h - half + 1, ov = cv - h - half + 1;
