@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--grid-deterministic", type=int, default=0, choices=[0, 1],
                     help="1: gridding sums in 64-bit fixed point (the same bits on every "
                          "run); 0: FP atomics (the default)")
+    ap.add_argument("--no-det-check", action="store_true",
+                    help="skip the deterministic-gridding comparison of the default run")
     ap.add_argument("--max-vis", type=int, default=0,
                     help="use only the first N visibilities (small profiling case)")
     args = ap.parse_args()
@@ -522,6 +524,35 @@ def run_ours(args, ws, rank, local):
                            "quadrature_points_per_vis": tap_nodes / (2 * args.steps * n_kept),
                            "rel_l2_vs_quadrature_path": rel_q}
 
+    # deterministic gridding beside the default: the same phi_grid call on a
+    # plan with 64-bit fixed-point grid sums, timed the same way, its bits
+    # compared across two calls and its image against the FP-atomic one
+    det_info = None
+    if not (args.grid_deterministic or args.no_det_check) and args.kernel_mode == "quadrature":
+        dplan = phi.Plan(uvw, **dict(desc, grid_deterministic=1))
+
+        def grid_ms(pl, reps=3):
+            out = []
+            for _ in range(reps):
+                flush_l2(flush)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                pl.grid(y_obs)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                out.append(e0.elapsed_time(e1))
+            return sum(out) / len(out)
+
+        d1 = dplan.grid(y_obs)
+        d2 = dplan.grid(y_obs)
+        dref = plan.grid(y_obs)
+        det_info = {"grid_call_ms": grid_ms(dplan), "fp_atomic_grid_call_ms": grid_ms(plan),
+                    "bitwise_repeatable": bool(torch.equal(d1, d2)),
+                    "rel_l2_vs_fp_atomic": float(torch.linalg.vector_norm((d1 - dref).double()) /
+                                                 torch.linalg.vector_norm(dref.double()))}
+        dplan.close()
+        del d1, d2, dref
+
     # roofline: the dominant kernel (fused quadrature + degrid or + grid)
     counts = load_oracle_counts()
     evals_per_vis = counts["evals_per_vis_mean"]
@@ -639,6 +670,7 @@ def run_ours(args, ws, rank, local):
         "kernel_mode": args.kernel_mode,
         "table": table_info,
         "radial": radial_info,
+        "deterministic_grid": det_info,
         "e2e": e2e,
         # this library's kernels in the timed steps (prep, fused degrid, fused
         # grid, finish: one each per stack group; with deterministic gridding

@@ -1666,166 +1666,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) vis_radial_kernel
   flush_counts(stats, my_bad, my_taps, my_nodes, lane);
 }
 
-// ---------------------------------------------------------------------------
-// Direction-dependent effects (Sec. 5.2)
-// ---------------------------------------------------------------------------
-
-// Degrid / grid with a separable DDE kernel D_i(s) = a_i(s_u) b_i(s_v)
-// (J_D = 2 h + 1 taps a side, caller's visibility order) convolved with the
-// w-kernel: the warp fills the visibility's J_w x J_w w-kernel taps into
-// shared memory -- by the per-tap quadrature, or (kRadial) from the radial
-// mode's series -- then forms every tap of the (J_w + J_D - 1)^2 box as
-// C(q) = sum_s D(s) [GC](u - q - s), i.e. from the stored taps K[q + s - q0].
-template <typename T, typename C, bool kGrid, bool kRadial>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) vis_dde_kernel(
-    const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
-    const C* __restrict__ grid_in, C* grid_out, const C* __restrict__ vis_in,
-    C* __restrict__ vis_out, QuadParams q, RadialView<T> rv, const C* __restrict__ dde_a,
-    const C* __restrict__ dde_b, int jd, int box_max, const int32_t* __restrict__ stack_slot,
-    unsigned long long* head, unsigned long long* stats, int batch) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31;
-  const int warp = threadIdx.x >> 5;
-  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
-  C* box = reinterpret_cast<C*>(smem_raw + (blockDim.x >> 5) * kNodeBatch * sizeof(NodeVal<T>)) +
-           warp * (box_max * box_max + 2 * jd + (kRadial ? rv.buf : 0));
-  C* dab = box + box_max * box_max;   // a_i then b_i
-  C* ser = dab + 2 * jd;              // kRadial: the visibility's series
-  // jd rows x 32 lanes of the row pass, in the node buffer (free once the
-  // box is complete; the next visibility rebuilds its nodes anyway)
-  C* ring = reinterpret_cast<C*>(sh);
-  static_assert(32 * 15 * sizeof(C) <= kNodeBatch * sizeof(NodeVal<T>),
-                "the row-pass ring of the largest DDE kernel must fit the node buffer");
-  const int h = jd >> 1;
-  unsigned long long my_bad = 0, my_taps = 0, my_nodes = 0;
-  const int npad = q.npad;
-  WarpQueue wq;
-  unsigned long long i;
-  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
-    const VisRec<T> r = recs[i];
-    const int Jw = r.jw;
-    const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
-    const int half = Jw / 2;
-    const T fu = r.fu, fv = r.fv;
-    const uint16_t* order = q.tap_order + q.tap_off[half - 1];
-    const float adw = static_cast<float>(fabs(r.dw));
-    int built = 0;
-    const uint32_t pm = perm[i];
-    const int64_t src = pm & 0x7fffffffu;
-    const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
-                       : cmake<C>(0.0, 0.0);
-    if (lane < 2 * jd) dab[lane] = lane < jd ? dde_a[src * jd + lane] : dde_b[src * jd + lane - jd];
-    const int ntap = Jw * Jw;
-    if (kRadial) {
-      // 1. the w-kernel on the J_w box from the visibility's series
-      const int pieces = radial_series<T, C>(ser, sh, q, rv, fu, fv, half, r.dw, lane, my_bad,
-                                             my_nodes);
-      const int last = pieces - 1;
-      const T last_f = static_cast<T>(last);
-      for (int t = lane; t < ntap; t += 32) {
-        const int kb = t / Jw, ka = t - kb * Jw;
-        const T du_ = fu - static_cast<T>(ka - half + 1), dv_ = fv - static_cast<T>(kb - half + 1);
-        box[t] = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
-      }
-    } else {
-      // 1. the w-kernel on the J_w box, by the per-tap quadrature: ring
-      // order, kVisTaps taps per lane, as in vis_kernel
-      for (int t0 = 0; t0 < ntap; t0 += 32 * kVisTaps) {
-        T rho[kVisTaps];
-        bool act[kVisTaps], ok[kVisTaps];
-        uint32_t code[kVisTaps];
-        T rmax = T(0);
-#pragma unroll
-        for (int k = 0; k < kVisTaps; ++k) {
-          const int t = t0 + 32 * k + lane;
-          act[k] = t < ntap;
-          code[k] = order[act[k] ? t : 0];
-          const T du_ = fu - static_cast<T>(static_cast<int>(code[k] & 0xffu) - half + 1);
-          const T dv_ = fv - static_cast<T>(static_cast<int>(code[k] >> 8) - half + 1);
-          rho[k] = sqrt(du_ * du_ + dv_ * dv_);
-          if (act[k]) rmax = fmax(rmax, rho[k]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-        const int npan = initial_panels(q, static_cast<float>(rmax), adw);
-        C K[kVisTaps];
-        eval_chunk_nt<kVisTaps>(sh, q, rho, act, r.dw, npan, kMaxPanels, built, ok, lane,
-                                my_nodes, K);
-#pragma unroll
-        for (int k = 0; k < kVisTaps; ++k)
-          if (act[k]) {
-            box[(code[k] >> 8) * Jw + (code[k] & 0xffu)] = K[k];
-            if (!ok[k]) ++my_bad;
-          }
-      }
-    }
-    __syncwarp();
-    // 2. the combined taps over the (J_w + 2 h)^2 box, by separability:
-    // C(cv, cu) = sum_sv b(sv) R(cv - h + sv, cu) with the row pass
-    // R(kb, cu) = sum_su a(su) K(kb, cu - h + su).  Each lane takes one
-    // column cu and a run of rows [r0, r1), walking down it: row kb of R is
-    // formed once, when the walk reaches it (the 2 h rows above r0 first),
-    // into slot kb mod jd of the lane's own ring column, and stays there
-    // while rows kb .. kb + 2 h read it.  Columns go 32 at a time; a block of
-    // nb < 32 columns splits its rows into 32 / nb runs so that the lanes
-    // stay busy.
-    C accv = cmake<C>(0.0, 0.0);
-    const int Jc = Jw + 2 * h;
-    for (int c0 = 0; c0 < Jc; c0 += 32) {
-      const int nb = min(32, Jc - c0);
-      const int runs = 32 / nb, len = (Jc + runs - 1) / runs;
-      const int run = lane / nb, cu = c0 + lane - run * nb;
-      const int r0 = run * len, r1 = min(Jc, r0 + len);
-      if (run >= runs || r0 >= r1) continue;
-      C* ring_l = ring + lane;
-      // row kb of R at column cu into its slot
-      auto row_pass = [&](int kb, int slot) {
-        C rv_ = cmake<C>(0.0, 0.0);
-        const C* krow = box + kb * Jw;
-        for (int s = 0; s < jd; ++s) {
-          const int ka = cu - 2 * h + s;
-          if (ka < 0 || ka >= Jw) continue;
-          const C kv = krow[ka];
-          const C av = dab[s];
-          rv_.x += av.x * kv.x - av.y * kv.y;
-          rv_.y += av.x * kv.y + av.y * kv.x;
-        }
-        ring_l[slot * 32] = rv_;
-      };
-      int slot = max(0, r0 - 2 * h) % jd;
-      for (int kb = max(0, r0 - 2 * h); kb < min(r0, Jw); ++kb) {
-        row_pass(kb, slot);
-        slot = slot + 1 == jd ? 0 : slot + 1;
-      }
-      for (int cv = r0; cv < r1; ++cv) {
-        if (cv < Jw) {
-          row_pass(cv, slot);
-          slot = slot + 1 == jd ? 0 : slot + 1;
-        }
-        // rows kb = cv - 2 h .. cv of R (b index kb - cv + 2 h), those in the box
-        const int lo = max(0, cv - 2 * h), hi = min(Jw - 1, cv);
-        C acc = cmake<C>(0.0, 0.0);
-        int sl = lo % jd;
-        for (int kb = lo; kb <= hi; ++kb) {
-          const C rv2 = ring_l[sl * 32];
-          const C bv = dab[jd + kb - cv + 2 * h];
-          acc.x += bv.x * rv2.x - bv.y * rv2.y;
-          acc.y += bv.x * rv2.y + bv.y * rv2.x;
-          sl = sl + 1 == jd ? 0 : sl + 1;
-        }
-        ++my_taps;
-        const int ou = cu - h - half + 1, ov = cv - h - half + 1;
-        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
-                           wrap_index(r.bu + ou, npad);
-        apply_tap<C, kGrid>(acc, gi, yv, grid_in, grid_out, q.fx, accv);
-      }
-    }
-    // the box and the DDE taps are rewritten for the next visibility
-    __syncwarp();
-    if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
-  }
-  flush_counts(stats, my_bad, my_taps, my_nodes, lane);
-}
+// Direction-dependent effects (Sec. 5.2): vis_dde_kernel
+#include "dde_kernel.cuh"
 
 // ---------------------------------------------------------------------------
 // Host side of the operator
@@ -2038,55 +1880,8 @@ struct DdeArgs {
   int jd;
 };
 
-// Shared memory of one warp of vis_dde_kernel: the quadrature nodes, the
-// w-kernel box of the plan's largest support and the two DDE kernels.
-template <typename T, typename C>
-size_t dde_warp_smem(const Plan& p, int jd) {
-  const size_t jmax = static_cast<size_t>(std::max(p.max_jw, 2));
-  const size_t ser = p.d.kernel_mode == PHI_KERNEL_RADIAL ? p.radial_buf : 0;
-  return kNodeBatch * sizeof(NodeVal<T>) + (jmax * jmax + 2 * jd + ser) * sizeof(C);
-}
-
-template <typename T, typename C, bool kGrid>
-int launch_dde(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, int g, const C* grids_in,
-               C* grids_out, const C* vis_in, C* vis_out, const DdeArgs& dde, cudaStream_t s) {
-  int dev = 0, optin = 0, per_sm_smem = 0, reserved = 0;
-  PHI_CUDA_TRY(cudaGetDevice(&dev));
-  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  PHI_CUDA_TRY(cudaDeviceGetAttribute(&per_sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
-                                      dev));
-  PHI_CUDA_TRY(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev));
-  // warps per block that keep the most warps resident per SM (the boxes are
-  // large: a block of 8 can leave most of an SM's shared memory unused)
-  const size_t per_warp = dde_warp_smem<T, C>(p, dde.jd);
-  int warps = 0, best = 0;
-  for (int w = 1; w <= kVisThreads / 32; ++w) {
-    const size_t blk = per_warp * w;
-    if (blk > static_cast<size_t>(optin)) break;
-    const int resident = w * static_cast<int>(per_sm_smem / (blk + reserved));
-    if (resident >= best) {
-      best = resident;
-      warps = w;
-    }
-  }
-  if (warps < 1) return PHI_ERR_SUPPORT;
-  const size_t smem = per_warp * warps;
-  const bool radial = p.d.kernel_mode == PHI_KERNEL_RADIAL;
-  auto kernel = radial ? vis_dde_kernel<T, C, kGrid, true> : vis_dde_kernel<T, C, kGrid, false>;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * warps, smem) !=
-          cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  const int blocks = per_sm * p.num_sms;
-  const RadialView<T> rv = radial ? radial_view<T, C>(p) : RadialView<T>{};
-  kernel<<<blocks, 32 * warps, smem, s>>>(
-      recs, p.perm + b0, nk, grids_in, grids_out, vis_in, vis_out, p.quad(), rv,
-      static_cast<const C*>(dde.a), static_cast<const C*>(dde.b), dde.jd, std::max(p.max_jw, 2),
-      p.stack_slot_dev, p.counters + g, p.counters + p.K, queue_batch(nk, blocks * warps));
-  PHI_CUDA_TRY(cudaGetLastError());
-  return PHI_OK;
-}
+// dde_warp_smem, launch_dde
+#include "dde_launch.cuh"
 
 template <typename T, typename C, bool kGrid>
 int launch_group_kernel(Plan& p, int g, const C* grids_in, C* grids_out, const C* vis_in,
