@@ -83,6 +83,8 @@ def parse():
                          "run); 0: FP atomics (the default)")
     ap.add_argument("--no-det-check", action="store_true",
                     help="skip the deterministic-gridding comparison of the default run")
+    ap.add_argument("--no-serve-check", action="store_true",
+                    help="skip the short FP32/FP64 serving stream of the default run")
     ap.add_argument("--max-vis", type=int, default=0,
                     help="use only the first N visibilities (small profiling case)")
     args = ap.parse_args()
@@ -648,6 +650,21 @@ def run_ours(args, ws, rank, local):
     # end to end through the public API from pinned host buffers
     e2e = run_e2e(phi, desc, uvw_np, x_np, args.e2e_steps, dev) if args.e2e_steps > 0 else None
 
+    # a short serving stream through the serving engine, FP32 and FP64 on the
+    # same requests (the full stream is --workload serve)
+    serving = None
+    if not args.no_serve_check and not args.max_vis and rank == 0:
+        from paper_1903_06555_gb300 import serve as S
+        serving = {"stream": "6 observations of 5e4-1.5e5 visibilities, 512^2-1024^2 images, "
+                             "|w|max 50-3000, arriving together; 4 slots; degrid + grid each"}
+        for prec in ("f32", "f64"):
+            reqs = serve_requests(6, seed=11, mmin=5e4, mmax=1.5e5, sizes=(512, 1024),
+                                  precision=prec)
+            for r in reqs:
+                r.raise_stacks = True
+            with S.Server(150 * 10 ** 9, slots=4) as srv:
+                serving[prec] = S.summarize(srv.run_stream(reqs, realtime=False), t_first=0.0)
+
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step_max, "higher_is_better": True,
@@ -672,6 +689,7 @@ def run_ours(args, ws, rank, local):
         "radial": radial_info,
         "deterministic_grid": det_info,
         "e2e": e2e,
+        "serving": serving,
         # this library's kernels in the timed steps (prep, fused degrid, fused
         # grid, finish: one each per stack group; with deterministic gridding
         # also the term bound, the exponent and the fixed-point conversion of

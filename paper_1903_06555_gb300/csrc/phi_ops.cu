@@ -1795,9 +1795,22 @@ int launch_tile_table(Plan& p, int k, const C* grids_in, C* grids_out, const C* 
   const int jmax = std::max(p.stack_jw[k], 2);
   const int side = p.tile + jmax;
   const size_t smem = sizeof(C) * static_cast<size_t>(side) * side;
-  PHI_CUDA_TRY(cudaFuncSetAttribute(tile_table_kernel<T, C, kGrid>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
+  int dev = 0, optin = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  PHI_CUDA_TRY(cudaFuncGetAttributes(&fa, tile_table_kernel<T, C, kGrid>));
+  if (smem + fa.sharedSizeBytes > static_cast<size_t>(optin)) {
+    // the patch does not fit a block: this stack's records unstaged
+    const int64_t b0 = p.stack_off[k], nk = p.stack_off[k + 1] - b0;
+    const int blocks = p.num_sms * 8;
+    vis_table_kernel<T, C, kGrid><<<blocks, kVisThreads, 0, s>>>(
+        static_cast<const VisRec<T>*>(p.recs) + b0, p.perm + b0, nk, grids_in, grids_out, vis_in,
+        vis_out, table_view<T, C>(p), p.npad, p.stack_slot_dev, p.counters + k, p.counters + p.K,
+        queue_batch(nk, blocks * (kVisThreads / 32)));
+    PHI_CUDA_TRY(cudaGetLastError());
+    return PHI_OK;
+  }
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_table_kernel<T, C, kGrid>,
                                                     kVisThreads, smem) != cudaSuccess ||
@@ -1828,12 +1841,11 @@ int launch_row_table(Plan& p, int g, const C* grids_in, C* grids_out, const C* v
   int dev = 0, optin = 0;
   PHI_CUDA_TRY(cudaGetDevice(&dev));
   PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-  if (smem > static_cast<size_t>(optin)) return PHI_OK;
+  cudaFuncAttributes fa;
+  PHI_CUDA_TRY(cudaFuncGetAttributes(&fa, row_table_kernel<T, C, kGrid>));
+  if (smem + fa.sharedSizeBytes > static_cast<size_t>(optin)) return PHI_OK;
   launched = true;
   if (ni == 0) return PHI_OK;
-  PHI_CUDA_TRY(cudaFuncSetAttribute(row_table_kernel<T, C, kGrid>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(smem)));
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, row_table_kernel<T, C, kGrid>,
                                                     kVisThreads, smem) != cudaSuccess ||
@@ -2112,6 +2124,26 @@ cudaError_t set_dde_smem(int bytes) {
   return e;
 }
 
+// The largest dynamic shared memory a block of `kernel` may use: the opt-in
+// limit less the kernel's static shared memory.
+template <typename K>
+cudaError_t set_max_dynamic_smem(K kernel, int optin) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              optin - static_cast<int>(fa.sharedSizeBytes));
+}
+
+template <typename T, typename C>
+cudaError_t set_staging_smem(int optin) {
+  cudaError_t e = set_max_dynamic_smem(tile_table_kernel<T, C, false>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(tile_table_kernel<T, C, true>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(row_table_kernel<T, C, false>, optin);
+  if (e == cudaSuccess) e = set_max_dynamic_smem(row_table_kernel<T, C, true>, optin);
+  return e;
+}
+
 int set_kernel_smem_limits() {
   const size_t f32 = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<float>);
   const size_t f64 = (kVisThreads / 32) * kNodeBatch * sizeof(NodeVal<double>);
@@ -2146,6 +2178,12 @@ int set_kernel_smem_limits() {
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
   PHI_CUDA_TRY((set_dde_smem<float, float2>(optin)));
   PHI_CUDA_TRY((set_dde_smem<double, double2>(optin)));
+  // table staging: patch and row sizes depend on the plan; the attribute is
+  // process-wide, so plans used from several threads at once all set the
+  // same value, the opt-in limit (larger patches and rows fall back to the
+  // unstaged kernel)
+  PHI_CUDA_TRY((set_staging_smem<float, float2>(optin)));
+  PHI_CUDA_TRY((set_staging_smem<double, double2>(optin)));
   return PHI_OK;
 }
 

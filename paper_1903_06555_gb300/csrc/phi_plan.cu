@@ -527,12 +527,15 @@ int build(Plan& p, const double* uvw, const double* weights, int64_t M, cudaStre
   if (wabs > 0.0) std::frexp(wabs, &E);
   const int S = 62 - E;
   const int64_t chunk = ((M + nblk - 1) / nblk + 31) / 32 * 32;
-  const size_t sweep_smem =
-      static_cast<size_t>(K) * ((kPlanThreads / 32) * kAcc * sizeof(unsigned long long) +
-                                sizeof(double) + 2 * sizeof(float));
+  const size_t sweep_per_stack = (kPlanThreads / 32) * kAcc * sizeof(unsigned long long) +
+                                 sizeof(double) + 2 * sizeof(float);
+  const size_t sweep_smem = static_cast<size_t>(K) * sweep_per_stack;
+  // The limit is a process-wide attribute of the function: a plan built at
+  // the same time on another thread must not lower it under this launch, so
+  // it is always set to what the most stacks a plan can have (126) need.
   PHI_CUDA_TRY(cudaFuncSetAttribute(kmeans_sweep_kernel,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(sweep_smem)));
+                                    static_cast<int>(126 * sweep_per_stack)));
   if (M > 0 && fixed_centres) {
     kmeans_sweep_kernel<<<nblk, kPlanThreads, sweep_smem, s>>>(w_fold, M, chunk, centres, K, S,
                                                                stack, nullptr, nullptr);

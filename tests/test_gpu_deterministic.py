@@ -84,9 +84,11 @@ def test_deterministic_table_grid(case, precision, staging):
     assert torch.equal(plan.grid(y), x1)
 
 
+@pytest.mark.parametrize("mode", ["quadrature", "radial"])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_deterministic_dde_grid(precision):
-    """DDE convolution (Sec. 5.2): the term bound includes the DDE kernels' sums."""
+def test_deterministic_dde_grid(precision, mode):
+    """DDE convolution (Sec. 5.2): the term bound includes the DDE kernels'
+    sums; both the whole-box (quadrature) and the banded (radial) kernel."""
     geo = oracle_geo(128)
     uvw = W.uvw_disk(600, 60.0, 40.0, 93)
     wts = np.linspace(0.5, 1.5, len(uvw))
@@ -94,11 +96,25 @@ def test_deterministic_dde_grid(precision):
     a, b = W.dde_kernels(len(uvw), 5, 94)
     yr = W.random_vis(len(uvw), 95)
     x_ref = O.grid_dde(op, yr, a, b)
-    plan = gpu_plan(uvw, geo, 3, False, precision, wts, grid_deterministic=1)
+    plan = gpu_plan(uvw, geo, 3, False, precision, wts, kernel_mode=mode, grid_deterministic=1)
     y = to_t(yr, ctype(precision))
     x1 = plan.grid_dde(y, a, b)
     assert O.rel_l2(x1.cpu().numpy(), x_ref) < gate(precision)
     assert torch.equal(plan.grid_dde(y, a, b), x1)
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_deterministic_grid_one_stack_per_group(case, precision):
+    """max_grid_mib = 1 leaves room for one grid and its fixed-point sums at a
+    time: every stack group sets its own exponent and converts its own sums,
+    and the result still matches the oracle and repeats bit for bit."""
+    plan = gpu_plan(case["uvw"], case["geo"], 3, True, precision, case["w"], max_grid_mib=1,
+                    grid_deterministic=1)
+    assert plan.info()["group"] == 1
+    y = to_t(case["yr"], ctype(precision))
+    x1 = plan.grid(y)
+    assert O.rel_l2(x1.cpu().numpy(), case["x_ref"]) < gate(precision)
+    assert torch.equal(plan.grid(y), x1)
 
 
 def test_degrid_is_unchanged_by_the_flag(case):

@@ -125,3 +125,36 @@ def test_admission_estimate_bounds_the_plan(image_n, k, m, raise_stacks):
         assert res.n_stacks > k
     io = m * 2 * 8 + image_n * image_n * 2 * 4
     assert res.device_bytes + io <= est, (res.device_bytes, est)
+
+
+def test_concurrent_plan_builds_with_different_stack_counts():
+    """Plans built at once on several host threads and streams, with K from 2
+    to 126 (the k-means sweep's shared memory grows with K past the 48 KB
+    default), all succeed and give the centres of the same plan built alone:
+    no build lowers a shared launch limit under another's launch."""
+    import threading
+    uvw = W.uvw_disk(20000, 60.0, 40.0, 3)
+    ks = [126, 2, 110, 8, 126, 4, 64, 120]
+    desc = dict(image_n=128, fov_rad=math.radians(20.0), conj_fold=1)
+    alone = {k: phi.Plan(torch.from_numpy(uvw), n_stacks=k, **desc).info()["wbar"]
+             for k in set(ks)}
+    for _ in range(3):
+        got, errors = [None] * len(ks), []
+
+        def build(j):
+            try:
+                s = torch.cuda.Stream()
+                with torch.cuda.stream(s):
+                    got[j] = phi.Plan(torch.from_numpy(uvw), stream=s, n_stacks=ks[j],
+                                      **desc).info()["wbar"]
+            except Exception as e:   # noqa: BLE001 - reported below
+                errors.append(repr(e))
+
+        threads = [threading.Thread(target=build, args=(j,)) for j in range(len(ks))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        assert not errors, errors
+        for j, k in enumerate(ks):
+            assert got[j] == alone[k]
