@@ -141,7 +141,8 @@ typedef struct {
                                2^61 from the call's largest |W_i y_i| (times
                                the DDE kernels' sums), the number of
                                visibilities in the stack group and a bound
-                               on |[GC]|; each term is off by at most 2^-e/2
+                               on |[GC]|, within the exponents of the grid's
+                               precision; each term is off by at most 2^-e/2
                                (far below FP32 rounding, and below 1e-10 of
                                the largest term times the visibility count
                                in FP64).  Costs 16 bytes per resident grid

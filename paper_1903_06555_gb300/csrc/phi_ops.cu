@@ -432,10 +432,11 @@ __global__ void fixed_bound_kernel(const VisRec<T>* __restrict__ recs,
 }
 
 // The exponent e of a call: every partial sum of a cell is at most
-// n_terms * bound * max factor, and e keeps that below 2^61 (clamped to
-// [-90, 120]); exp[1] = 1 for a non-finite factor.
+// n_terms * bound * max factor, and e keeps that below 2^61, within
+// [emin, emax] (the range where 2^(32 - e) and 2^-e are numbers of the
+// grid's precision); exp[1] = 1 for a non-finite factor.
 __global__ void fixed_exp_kernel(const unsigned long long* __restrict__ maxbits, double scale,
-                                 int* __restrict__ exp) {
+                                 int emin, int emax, int* __restrict__ exp) {
   const double A = __longlong_as_double(static_cast<long long>(*maxbits)) * scale;
   if (!isfinite(A)) {
     exp[0] = 0;
@@ -444,7 +445,7 @@ __global__ void fixed_exp_kernel(const unsigned long long* __restrict__ maxbits,
   }
   int ex = 0;
   if (A > 0.0) frexp(A, &ex);   // A < 2^ex
-  exp[0] = min(max(61 - ex, -90), 120);
+  exp[0] = min(max(61 - ex, emin), emax);
   exp[1] = 0;
 }
 
@@ -2004,7 +2005,11 @@ int fixed_prepare(Plan& p, int g, const C* y, const DdeArgs* dde, cudaStream_t s
   const double periods = std::ceil(static_cast<double>(jbox) / p.npad);
   const double scale = 4.0 * p.kernel_bound * static_cast<double>(std::max<int64_t>(nk, 1)) *
                        periods * periods;
-  fixed_exp_kernel<<<1, 1, 0, s>>>(p.fx_max, scale, p.fx_exp);
+  // FP32 grids: 2^(32 - e) below FLT_MAX and 2^-e not below the smallest
+  // subnormal; FP64 likewise for doubles
+  const bool f64 = sizeof(T) == 8;
+  fixed_exp_kernel<<<1, 1, 0, s>>>(p.fx_max, scale, f64 ? -990 : -95, f64 ? 1070 : 149,
+                                   p.fx_exp);
   PHI_CUDA_TRY(cudaGetLastError());
   return PHI_OK;
 }

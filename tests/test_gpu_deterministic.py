@@ -7,8 +7,8 @@ quadrature and radial modes, the table path (against the oracle's own table
 path) and the DDE convolution; identical bits on repeated calls and across
 plans; agreement with the FP-atomic gridder; degridding untouched by the
 flag; the exponent chosen from the data (visibilities scaled by 1e-20 and
-1e20 grid to the scaled image); a non-finite visibility gives a NaN image
-rather than wrapped integers."""
+1e20, 1e-150 and 1e150 in FP64, grid to the scaled image); a non-finite
+visibility gives a NaN image rather than wrapped integers."""
 import math
 
 import numpy as np
@@ -135,17 +135,19 @@ def test_deterministic_adjoint_dot_product(case, precision):
     assert abs(lhs - rhs) <= (1e-12 if precision == "f64" else 2e-5) * abs(lhs)
 
 
-@pytest.mark.parametrize("scale", [1e-20, 1e20])
-def test_exponent_follows_the_data(case, scale):
-    """Linearity across 40 decades: the fixed-point exponent is chosen per
-    call from the largest term, so scaled visibilities grid to the scaled
-    image within the FP32 gate."""
-    plan = gpu_plan(case["uvw"], case["geo"], 3, True, "f32", case["w"], grid_deterministic=1)
-    y = to_t(case["yr"], torch.complex64)
+@pytest.mark.parametrize("precision,scale", [("f32", 1e-20), ("f32", 1e20), ("f64", 1e-150),
+                                             ("f64", 1e150)])
+def test_exponent_follows_the_data(case, precision, scale):
+    """Linearity across 40 (FP32) and 300 (FP64) decades: the fixed-point
+    exponent is chosen per call from the largest term, so scaled visibilities
+    grid to the scaled image within the gate."""
+    plan = gpu_plan(case["uvw"], case["geo"], 3, True, precision, case["w"],
+                    grid_deterministic=1)
+    y = to_t(case["yr"], ctype(precision))
     x = plan.grid(y).double()
     xs = plan.grid(y * scale).double() / scale
     assert torch.isfinite(xs).all()
-    assert (torch.linalg.norm(xs - x) / torch.linalg.norm(x)).item() < TOL32
+    assert (torch.linalg.norm(xs - x) / torch.linalg.norm(x)).item() < gate(precision)
 
 
 def test_non_finite_visibility_gives_nan_image(case):
