@@ -208,3 +208,147 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) vis_dde_kernel(
   }
   flush_counts(stats, my_bad, my_taps, my_nodes, lane);
 }
+
+// Two-pass DDE convolution of quadrature plans.  A whole w-kernel box in
+// shared memory (11.5 KB at J_w = 38) leaves room for few warps per SM,
+// which starves the quadrature of the latency hiding it needs, so when that
+// happens the box goes through global memory instead: dde_box_kernel
+// integrates the boxes of a chunk of visibilities with vis_kernel's warp
+// layout and occupancy (node buffer only), and dde_conv_kernel forms their
+// combined taps with the separable passes and applies them, holding only
+// the DDE kernels and the row-pass ring in shared memory.
+
+// Pass 1: the J_w x J_w w-kernel box of each of records [0, n) into
+// boxes[i * jmax^2], row-major with row length J_w.
+template <typename T, typename C>
+__global__ void __launch_bounds__(VisLaunch<T>::threads, VisLaunch<T>::min_blocks)
+    dde_box_kernel(const VisRec<T>* __restrict__ recs, int64_t n, C* __restrict__ boxes,
+                   int jmax, QuadParams q, unsigned long long* head,
+                   unsigned long long* stats, int batch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
+  unsigned long long my_bad = 0, my_nodes = 0;
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw, half = Jw / 2, ntap = Jw * Jw;
+    C* box = boxes + static_cast<int64_t>(i) * jmax * jmax;
+    const T fu = r.fu, fv = r.fv;
+    const uint16_t* order = q.tap_order + q.tap_off[half - 1];
+    const float adw = static_cast<float>(fabs(r.dw));
+    int built = 0;
+    for (int t0 = 0; t0 < ntap; t0 += 32 * kVisTaps) {
+      T rho[kVisTaps];
+      bool act[kVisTaps], ok[kVisTaps];
+      uint32_t code[kVisTaps];
+      T rmax = T(0);
+#pragma unroll
+      for (int k = 0; k < kVisTaps; ++k) {
+        const int t = t0 + 32 * k + lane;
+        act[k] = t < ntap;
+        code[k] = order[act[k] ? t : 0];
+        const T du_ = fu - static_cast<T>(static_cast<int>(code[k] & 0xffu) - half + 1);
+        const T dv_ = fv - static_cast<T>(static_cast<int>(code[k] >> 8) - half + 1);
+        rho[k] = sqrt(du_ * du_ + dv_ * dv_);
+        if (act[k]) rmax = fmax(rmax, rho[k]);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+      const int npan = initial_panels(q, static_cast<float>(rmax), adw);
+      C K[kVisTaps];
+      eval_chunk_nt<kVisTaps>(sh, q, rho, act, r.dw, npan, kMaxPanels, built, ok, lane, my_nodes,
+                              K);
+#pragma unroll
+      for (int k = 0; k < kVisTaps; ++k)
+        if (act[k]) {
+          box[(code[k] >> 8) * Jw + (code[k] & 0xffu)] = K[k];
+          if (!ok[k]) ++my_bad;
+        }
+    }
+  }
+  // unconverged taps and tap-node evaluations into the statistics (the taps
+  // themselves are counted by pass 2, as combined taps)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
+    my_nodes += __shfl_xor_sync(0xffffffffu, my_nodes, o);
+  }
+  if (lane == 0) {
+    if (my_bad) atomicAdd(stats, my_bad);
+    if (my_nodes) atomicAdd(stats + 3, my_nodes);
+  }
+}
+
+// Pass 2: records [0, n) with their boxes from pass 1; the combined taps by
+// the separable passes, each lane one column and a run of rows with its
+// ring column in shared memory (jd x 32 per warp, after the warp's DDE
+// kernels), exactly as vis_dde_kernel's quadrature branch.
+template <typename T, typename C, bool kGrid>
+__global__ void __launch_bounds__(256) dde_conv_kernel(
+    const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
+    const C* __restrict__ boxes, int jmax, const C* __restrict__ grid_in, C* grid_out,
+    const C* __restrict__ vis_in, C* __restrict__ vis_out, const C* __restrict__ dde_a,
+    const C* __restrict__ dde_b, int jd, int npad, FixedGrid fx,
+    const int32_t* __restrict__ stack_slot, unsigned long long* head,
+    unsigned long long* stats, int batch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  C* dab = reinterpret_cast<C*>(smem_raw) + warp * (2 * jd + 32 * jd);   // a_i then b_i
+  C* ring = dab + 2 * jd;
+  const int h = jd >> 1;
+  unsigned long long my_taps = 0;
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw, Jc = Jw + 2 * h, half = Jw / 2;
+    const C* __restrict__ box = boxes + static_cast<int64_t>(i) * jmax * jmax;
+    const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
+    const uint32_t pm = perm[i];
+    const int64_t src = pm & 0x7fffffffu;
+    const C yv = kGrid ? load_visibility<T, C>(vis_in, pm, static_cast<T>(r.weight))
+                       : cmake<C>(0.0, 0.0);
+    if (lane < 2 * jd) dab[lane] = lane < jd ? dde_a[src * jd + lane] : dde_b[src * jd + lane - jd];
+    __syncwarp();
+    C accv = cmake<C>(0.0, 0.0);
+    for (int c0 = 0; c0 < Jc; c0 += 32) {
+      const int nb = min(32, Jc - c0);
+      const int runs = 32 / nb, len = (Jc + runs - 1) / runs;
+      const int run = lane / nb, cu = c0 + lane - run * nb;
+      const int r0 = run * len, r1 = min(Jc, r0 + len);
+      if (run >= runs || r0 >= r1) continue;
+      C* ring_l = ring + lane;
+      int slot = max(0, r0 - 2 * h) % jd;
+      auto row_pass = [&](int kb) {
+        C acc = cmake<C>(0.0, 0.0);
+        for (int s = 0; s < jd; ++s) {
+          const int ka = cu - 2 * h + s;
+          if (ka >= 0 && ka < Jw) cmad(acc, dab[s], box[kb * Jw + ka]);
+        }
+        ring_l[slot * 32] = acc;
+        slot = slot + 1 == jd ? 0 : slot + 1;
+      };
+      for (int kb = max(0, r0 - 2 * h); kb < min(r0, Jw); ++kb) row_pass(kb);
+      for (int cv = r0; cv < r1; ++cv) {
+        if (cv < Jw) row_pass(cv);
+        const int lo = max(0, cv - 2 * h), hi = min(Jw - 1, cv);
+        C acc = cmake<C>(0.0, 0.0);
+        for (int kb = lo, sl = lo % jd; kb <= hi; ++kb, sl = sl + 1 == jd ? 0 : sl + 1)
+          cmad(acc, dab[jd + kb - cv + 2 * h], ring_l[sl * 32]);
+        ++my_taps;
+        const int ou = cu - h - half + 1, ov = cv - h - half + 1;
+        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
+                           wrap_index(r.bu + ou, npad);
+        apply_tap<C, kGrid>(acc, gi, yv, grid_in, grid_out, fx, accv);
+      }
+    }
+    // the DDE taps and the ring are rewritten for the next visibility
+    __syncwarp();
+    if (!kGrid) store_visibility<T, C>(accv, static_cast<T>(r.weight), pm, vis_out, lane);
+  }
+  flush_counts(stats, 0, my_taps, 0, lane);
+}

@@ -130,3 +130,48 @@ def test_dde_mwa_snapshot_unfolded_at_full_size():
                                 plan.degrid_dde(xr, a, b).to(torch.complex128))).item()
     rhs = torch.sum(xr.double() * plan.grid_dde(yv, a, b).double()).item()
     assert abs(lhs - rhs) <= 1e-4 * abs(lhs)
+
+
+@pytest.fixture(scope="module")
+def wide():
+    """Supports of 38 taps (w up to 60 wavelengths in one stack): a whole
+    w-kernel box per warp in shared memory would leave fewer than 24 warps
+    per SM, so these plans take the two-pass path (boxes through a transient
+    global buffer, then the separable convolution)."""
+    geo = oracle_geo(128)
+    uvw = W.uvw_disk(120, 60.0, 60.0, 81)
+    wts = np.linspace(0.5, 1.5, len(uvw))
+    op = O.make_plan(uvw, geo, 1, False, weights=wts)
+    a, b = W.dde_kernels(len(uvw), 5, 82)
+    x = W.point_sources(128, 20, 83)
+    yr = W.random_vis(len(uvw), 84)
+    return dict(geo=geo, uvw=uvw, w=wts, op=op, a=a, b=b, x=x, yr=yr,
+                y_ref=O.degrid_dde(op, x, a, b), x_ref=O.grid_dde(op, yr, a, b))
+
+
+@pytest.mark.parametrize("precision", ["f32", "f64"])
+def test_dde_two_pass_matches_oracle(wide, precision):
+    plan = gpu_plan(wide["uvw"], wide["geo"], 1, False, precision, wide["w"])
+    jw = plan.info()["max_jw"]
+    assert jw >= 30
+    rd, cd, tol = dtypes(precision)
+    y = plan.degrid_dde(to_t(wide["x"], rd), wide["a"], wide["b"]).cpu().numpy()
+    assert O.rel_l2(y, wide["y_ref"]) < tol
+    x = plan.grid_dde(to_t(wide["yr"], cd), wide["a"], wide["b"]).cpu().numpy()
+    assert O.rel_l2(x, wide["x_ref"]) < tol
+    bad, taps = plan.stats()
+    kept = int((~wide["op"].dropped).sum())
+    assert bad == 0 and taps == 2 * kept * (jw + 4) ** 2
+
+
+def test_dde_two_pass_delta_is_the_plain_operator(wide):
+    """J_D = 1 with a = b = 1 through the two-pass path is phi_degrid /
+    phi_grid (the boxes' taps are the plain kernel's, in another order of
+    summation)."""
+    plan = gpu_plan(wide["uvw"], wide["geo"], 1, False, "f32")
+    n = len(wide["uvw"])
+    one = np.ones((n, 1), np.complex64)
+    x = to_t(wide["x"], torch.float32)
+    assert O.rel_l2(plan.degrid_dde(x, one, one).cpu().numpy(), plan.degrid(x).cpu().numpy()) < 1e-6
+    y = to_t(wide["yr"], torch.complex64)
+    assert O.rel_l2(plan.grid_dde(y, one, one).cpu().numpy(), plan.grid(y).cpu().numpy()) < 1e-6
