@@ -46,7 +46,9 @@
  * Memory and streams: every pointer argument named *_dev is a device pointer
  * owned by the caller; the plan owns everything it allocates (sorted
  * visibility records, permutation, stack tables, per-pixel factors, the
- * padded grids of one group of stacks, cuFFT plans and their workspace).  Calls are asynchronous on the
+ * padded grids of one group of stacks, cuFFT plans and their workspace);
+ * the DDE calls may also take a transient buffer (see phi_degrid_dde).
+ * Calls are asynchronous on the
  * given stream (a cudaStream_t passed as void*; NULL = legacy default stream)
  * and do not synchronise, except phi_plan_create (it reads the k-means
  * convergence test back every sweep) and the calls that return host values
@@ -311,6 +313,12 @@ int phi_grid(phi_plan_t plan, const void* vis_dev, void* image_dev, void* stream
  * PHI_ERR_SUPPORT if one warp's w-kernel box for the plan's largest support
  * does not fit in a thread block's shared memory.  No counterpart for the
  * kernels' values: the paper gives no DDE model; they are the caller's.
+ * Memory: in a quadrature plan whose largest box would leave few warps per
+ * SM (J_w above about 24 in FP32, 10 in FP64) the boxes go through a
+ * transient device buffer of at most 2 GiB, taken with cudaMallocAsync and
+ * given back with cudaFreeAsync on `stream` (stream-ordered: no device-wide
+ * synchronisation); when it cannot be had the call runs single-pass, with
+ * the box in shared memory.  Nothing else is allocated.
  */
 int phi_degrid_dde(phi_plan_t plan, const void* image_dev, const void* dde_a_dev,
                    const void* dde_b_dev, int32_t dde_taps, void* vis_dev, void* stream);
