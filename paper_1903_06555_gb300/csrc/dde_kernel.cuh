@@ -209,14 +209,15 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 2) vis_dde_kernel(
   flush_counts(stats, my_bad, my_taps, my_nodes, lane);
 }
 
-// Two-pass DDE convolution of quadrature plans.  A whole w-kernel box in
-// shared memory (11.5 KB at J_w = 38) leaves room for few warps per SM,
-// which starves the quadrature of the latency hiding it needs, so when that
-// happens the box goes through global memory instead: dde_box_kernel
-// integrates the boxes of a chunk of visibilities with vis_kernel's warp
-// layout and occupancy (node buffer only), and dde_conv_kernel forms their
-// combined taps with the separable passes and applies them, holding only
-// the DDE kernels and the row-pass ring in shared memory.
+// Two-pass DDE convolution.  A whole w-kernel box in shared memory (11.5 KB
+// at J_w = 38), or a band of it with its ring, leaves room for few warps per
+// SM, which starves the quadrature of the latency hiding it needs, so when
+// that happens the box goes through global memory instead: dde_box_kernel
+// (or dde_box_radial_kernel in radial mode) computes the boxes of a chunk of
+// visibilities with the plain kernel's warp layout and occupancy, and
+// dde_conv_kernel forms their combined taps with the separable passes and
+// applies them, holding only the DDE kernels and the row-pass ring in
+// shared memory.
 
 // Pass 1: the J_w x J_w w-kernel box of each of records [0, n) into
 // boxes[i * jmax^2], row-major with row length J_w.
@@ -271,6 +272,50 @@ __global__ void __launch_bounds__(VisLaunch<T>::threads, VisLaunch<T>::min_block
   }
   // unconverged taps and tap-node evaluations into the statistics (the taps
   // themselves are counted by pass 2, as combined taps)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);
+    my_nodes += __shfl_xor_sync(0xffffffffu, my_nodes, o);
+  }
+  if (lane == 0) {
+    if (my_bad) atomicAdd(stats, my_bad);
+    if (my_nodes) atomicAdd(stats + 3, my_nodes);
+  }
+}
+
+// Pass 1 in radial mode: each visibility's series (radial_series, with
+// vis_radial_kernel's block shape: node buffers, then a series buffer per
+// warp), then its box from the series, row-major with row length J_w.
+template <typename T, typename C>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) dde_box_radial_kernel(
+    const VisRec<T>* __restrict__ recs, int64_t n, C* __restrict__ boxes, int jmax, QuadParams q,
+    RadialView<T> rv, unsigned long long* head, unsigned long long* stats, int batch) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  NodeVal<T>* sh = reinterpret_cast<NodeVal<T>*>(smem_raw) + warp * kNodeBatch;
+  C* ser = reinterpret_cast<C*>(smem_raw + (blockDim.x >> 5) * kNodeBatch * sizeof(NodeVal<T>)) +
+           warp * rv.buf;
+  unsigned long long my_bad = 0, my_nodes = 0;
+  WarpQueue wq;
+  unsigned long long i;
+  while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
+    const VisRec<T> r = recs[i];
+    const int Jw = r.jw, half = Jw / 2, ntap = Jw * Jw;
+    C* box = boxes + static_cast<int64_t>(i) * jmax * jmax;
+    const T fu = r.fu, fv = r.fv;
+    const int last =
+        radial_series<T, C>(ser, sh, q, rv, fu, fv, half, r.dw, lane, my_bad, my_nodes) - 1;
+    const T last_f = static_cast<T>(last);
+    for (int t = lane; t < ntap; t += 32) {
+      const int kb = t / Jw, ka = t - kb * Jw;
+      const T du_ = fu - static_cast<T>(ka - half + 1);
+      const T dv_ = fv - static_cast<T>(kb - half + 1);
+      box[t] = radial_eval<T, C>(ser, rv, last, last_f, sqrt(du_ * du_ + dv_ * dv_));
+    }
+    // the series is rewritten for the next visibility
+    __syncwarp();
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     my_bad += __shfl_xor_sync(0xffffffffu, my_bad, o);

@@ -16,8 +16,8 @@ size_t dde_warp_smem(const Plan& p, int jd) {
              sizeof(C);
 }
 
-// Quadrature plans whose single-pass DDE kernel would keep fewer warps than
-// this resident per SM take the two-pass path; its transient box buffer
+// Plans whose single-pass DDE kernel would keep fewer warps than this
+// resident per SM take the two-pass path; its transient box buffer
 // holds at most kDdeBoxBytes (chunks of visibilities otherwise).
 constexpr int kDdeTwoPassWarps = 24;
 constexpr size_t kDdeBoxBytes = size_t(2) << 30;
@@ -43,18 +43,29 @@ int launch_dde_two_pass(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, 
   }
   PHI_CUDA_TRY(ea);
   launched = true;
-  // pass 1: vis_kernel's block shape and node buffer (a constant limit for
-  // all plans, so concurrent launchers agree)
+  // pass 1: the plain kernel's block shape and shared memory (limits set
+  // to one value for all plans, so concurrent launchers agree)
+  const bool radial = p.d.kernel_mode == PHI_KERNEL_RADIAL;
   constexpr int box_threads = VisLaunch<T>::threads;
-  const size_t box_smem = (box_threads / 32) * kNodeBatch * sizeof(NodeVal<T>);
-  PHI_CUDA_TRY(cudaFuncSetAttribute(dde_box_kernel<T, C>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    static_cast<int>(box_smem)));
+  const size_t box_smem = radial ? radial_smem<T, C>(p)
+                                 : (box_threads / 32) * kNodeBatch * sizeof(NodeVal<T>);
+  int dev = 0, optin = 0;
+  PHI_CUDA_TRY(cudaGetDevice(&dev));
+  PHI_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (radial)
+    PHI_CUDA_TRY(cudaFuncSetAttribute(dde_box_radial_kernel<T, C>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, optin));
+  else
+    PHI_CUDA_TRY(cudaFuncSetAttribute(
+        dde_box_kernel<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        static_cast<int>((box_threads / 32) * kNodeBatch * sizeof(NodeVal<T>))));
   int box_per_sm = 0, conv_per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&box_per_sm, dde_box_kernel<T, C>,
-                                                    box_threads, box_smem) != cudaSuccess ||
-      box_per_sm < 1)
-    box_per_sm = 1;
+  const cudaError_t eo =
+      radial ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                   &box_per_sm, dde_box_radial_kernel<T, C>, box_threads, box_smem)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&box_per_sm, dde_box_kernel<T, C>,
+                                                             box_threads, box_smem);
+  if (eo != cudaSuccess || box_per_sm < 1) box_per_sm = 1;
   // pass 2: the DDE kernels (2 jd) and the ring (32 jd) per warp; the limit
   // is that of the largest jd (15), the same for every plan
   const size_t conv_smem = (kVisThreads / 32) * 34 * static_cast<size_t>(dde.jd) * sizeof(C);
@@ -74,9 +85,14 @@ int launch_dde_two_pass(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, 
       st = PHI_ERR_CUDA;
       break;
     }
-    dde_box_kernel<T, C><<<box_blocks, box_threads, box_smem, s>>>(
-        recs + c0, n, boxes, jmax, p.quad(), head, p.counters + p.K,
-        queue_batch(n, box_blocks * (box_threads / 32)));
+    if (radial)
+      dde_box_radial_kernel<T, C><<<box_blocks, box_threads, box_smem, s>>>(
+          recs + c0, n, boxes, jmax, p.quad(), radial_view<T, C>(p), head, p.counters + p.K,
+          queue_batch(n, box_blocks * (box_threads / 32)));
+    else
+      dde_box_kernel<T, C><<<box_blocks, box_threads, box_smem, s>>>(
+          recs + c0, n, boxes, jmax, p.quad(), head, p.counters + p.K,
+          queue_batch(n, box_blocks * (box_threads / 32)));
     if (cudaGetLastError() != cudaSuccess ||
         cudaMemsetAsync(head, 0, sizeof(unsigned long long), s) != cudaSuccess) {
       st = PHI_ERR_CUDA;
@@ -117,7 +133,7 @@ int launch_dde(Plan& p, const VisRec<T>* recs, int64_t b0, int64_t nk, int g, co
     }
   }
   const bool radial = p.d.kernel_mode == PHI_KERNEL_RADIAL;
-  if (!radial && best < kDdeTwoPassWarps) {
+  if (best < kDdeTwoPassWarps) {
     bool launched = false;
     PHI_TRY_ST((launch_dde_two_pass<T, C, kGrid>(p, recs, b0, nk, g, grids_in, grids_out, vis_in,
                                                  vis_out, dde, s, launched)));

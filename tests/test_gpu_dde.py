@@ -149,9 +149,12 @@ def wide():
                 y_ref=O.degrid_dde(op, x, a, b), x_ref=O.grid_dde(op, yr, a, b))
 
 
+@pytest.mark.parametrize("mode", ["quadrature", "radial"])
 @pytest.mark.parametrize("precision", ["f32", "f64"])
-def test_dde_two_pass_matches_oracle(wide, precision):
-    plan = gpu_plan(wide["uvw"], wide["geo"], 1, False, precision, wide["w"])
+def test_dde_two_pass_matches_oracle(wide, precision, mode):
+    """Boxes by the per-tap quadrature or (radial) from the series, through
+    the two-pass path, against the oracle at the quadrature path's gates."""
+    plan = gpu_plan(wide["uvw"], wide["geo"], 1, False, precision, wide["w"], kernel_mode=mode)
     jw = plan.info()["max_jw"]
     assert jw >= 30
     rd, cd, tol = dtypes(precision)
