@@ -1137,6 +1137,14 @@ def run_diff(args):
     print(json.dumps(line), flush=True)
 
 
+def dde_macs(counts, jws, jd):
+    """Complex multiply-adds of the separable DDE convolution per call: per
+    visibility of support J_w, J_D J_w^2 in the row pass (each w-kernel tap
+    feeds J_D columns) and J_D J_w (J_w + J_D - 1) in the column pass (each
+    row of R feeds J_D combined rows, over J_w + J_D - 1 columns)."""
+    return sum(c * jd * j * (j + j + jd - 1) for c, j in zip(counts, jws))
+
+
 def run_dde(args):
     """Direction-dependent effects (Sec. 5.2): the MWA-like snapshot without
     the fold (16 stacks), a synthetic separable DDE kernel of 5 x 5 taps per
@@ -1182,7 +1190,7 @@ def run_dde(args):
     # visibility of support J_w, J_D J_w^2 for the row pass (J_w rows of the
     # J_w + J_D - 1 columns, J_D taps inside the box per w-kernel tap) and
     # J_D J_w (J_w + J_D - 1) for the column pass
-    macs = sum(c * jd * j * (j + j + jd - 1) for c, j in zip(info["counts"], info["jw"]))
+    macs = dde_macs(info["counts"], info["jw"], jd)
     flops = nodes * FLOPS_PER_TAP_NODE / calls + macs * 8.0
     ach = flops / (ms_dde / 2 / 1e3) / 1e12
     peaks = measured_peaks()

@@ -1,6 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the count of grid cells the
-kernel boxes cover (the grid part of the table kernel's minimum HBM bytes),
-against brute-force enumeration of every box."""
+kernel boxes cover (the grid part of the minimum HBM bytes), against
+brute-force enumeration of every box; the DDE convolution's multiply-add
+count, against enumeration of its terms."""
 import os
 import sys
 
@@ -41,3 +42,20 @@ def test_covered_grid_cells_against_brute_force():
     info = {"npad": npad, "du": du, "wbar": [3.0, 17.0, 33.0], "jw": [4, 6, 10]}
     for fold in (True, False):
         assert bench.covered_grid_cells(uvw, info, fold) == brute_cells(uvw, info, fold)
+
+
+def test_dde_multiply_add_count_matches_enumeration():
+    """The DDE roofline's work: the separable passes' complex multiply-adds,
+    counted term by term (terms outside the box left out, as the kernels do)
+    against the closed form bench.py uses."""
+    for J in (2, 4, 8, 38):
+        for jd in (1, 3, 5, 15):
+            h = jd // 2
+            Jc = J + 2 * h
+            row = sum(1 for kb in range(J) for cu in range(Jc) for s in range(jd)
+                      if 0 <= cu - 2 * h + s < J)
+            col = sum(1 for cv in range(Jc) for cu in range(Jc)
+                      for kb in range(max(0, cv - 2 * h), min(J - 1, cv) + 1))
+            assert bench.dde_macs([1], [J], jd) == row + col
+    assert bench.dde_macs([3, 2], [4, 8], 5) == 3 * bench.dde_macs([1], [4], 5) + \
+        2 * bench.dde_macs([1], [8], 5)
