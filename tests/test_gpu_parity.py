@@ -284,16 +284,33 @@ def test_mwa_snapshot_sampled_parity(mwa):
 
 
 def test_mwa_snapshot_adjoint_at_full_size(mwa):
-    """<Phi x, y> = <x, Phi^H y> at full size in FP32, to the 1e-5 of the
-    FP32 gate: both sides use the same kernel values, so only FP32 rounding
-    (FFTs, tap sums, atomics, the two inner products) separates them."""
+    """<Phi x, y> = <x, Phi^H y> at full size in FP32.  Both sides use the
+    same kernel values, so only FP32 rounding separates them.  With
+    deterministic gridding (64-bit fixed-point cell sums) that is the tap
+    sums and FFTs, and the gap is held to the FP32 gate, 1e-5 of
+    |<y, Phi x>| (measured 4.3e-6, the same on every run).  The default
+    gridder adds each cell's 1,000-2,500 contributions with FP32 atomics in
+    run-dependent order, and random x and y make <y, Phi x> cancel about
+    24,000-fold (|<y, Phi x>| ~ 4e-5 |y| |Phi x|), so that rounding moves
+    the gap from run to run (measured 3.5e-7 to 1.1e-5 of |<y, Phi x>|,
+    1.5e-11 to 4.5e-10 of |y| |Phi x|): it is held to 2e-9 of the
+    Cauchy-Schwarz scale |y| |Phi x|."""
     wl, uvw, geo, _ = mwa
-    plan = gpu_plan(uvw, geo, wl.n_stacks, wl.conj_fold, "f32")
     x = to_t(W.random_image(wl.image_n, 5), torch.float32)
     y = to_t(W.random_vis(len(uvw), 6), torch.complex64)
-    lhs = torch.real(torch.vdot(y.to(torch.complex128), plan.degrid(x).to(torch.complex128))).item()
-    rhs = torch.sum(x.double() * plan.grid(y).double()).item()
-    assert abs(lhs - rhs) <= TOL32 * abs(lhs)
+    for deterministic in (1, 0):
+        plan = gpu_plan(uvw, geo, wl.n_stacks, wl.conj_fold, "f32",
+                        grid_deterministic=deterministic)
+        yd = plan.degrid(x).to(torch.complex128)
+        lhs = torch.real(torch.vdot(y.to(torch.complex128), yd)).item()
+        rhs = torch.sum(x.double() * plan.grid(y).double()).item()
+        if deterministic:
+            assert abs(lhs - rhs) <= TOL32 * abs(lhs)
+        else:
+            scale = (torch.linalg.vector_norm(y.to(torch.complex128)) *
+                     torch.linalg.vector_norm(yd)).item()
+            assert abs(lhs - rhs) <= 2e-9 * scale
+        plan.close()
 
 
 @pytest.mark.parametrize("mode", ["quadrature", "table"])
