@@ -330,7 +330,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) dde_box_radial_ke
 // Pass 2: records [0, n) with their boxes from pass 1; the combined taps by
 // the separable passes, each lane one column and a run of rows with its
 // ring column in shared memory (jd x 32 per warp, after the warp's DDE
-// kernels), exactly as vis_dde_kernel's quadrature branch.
+// kernels).  A lane's grid column is fixed for its run and its grid row
+// advances by one per combined row, so neither is wrapped per tap.
 template <typename T, typename C, bool kGrid>
 __global__ void __launch_bounds__(256) dde_conv_kernel(
     const VisRec<T>* __restrict__ recs, const uint32_t* __restrict__ perm, int64_t n,
@@ -343,15 +344,24 @@ __global__ void __launch_bounds__(256) dde_conv_kernel(
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   C* dab = reinterpret_cast<C*>(smem_raw) + warp * (2 * jd + 32 * jd);   // a_i then b_i
-  C* ring = dab + 2 * jd;
-  const int h = jd >> 1;
+  C* ring_l = dab + 2 * jd + lane;                                       // this lane's column
+  const C* dbv = dab + jd;
+  const int h = jd >> 1, h2 = 2 * h;
   unsigned long long my_taps = 0;
   WarpQueue wq;
   unsigned long long i;
   while (wq.take(head, static_cast<unsigned long long>(batch), n, lane, i)) {
     const VisRec<T> r = recs[i];
-    const int Jw = r.jw, Jc = Jw + 2 * h, half = Jw / 2;
+    const int Jw = r.jw, Jc = Jw + h2, half = Jw / 2;
     const C* __restrict__ box = boxes + static_cast<int64_t>(i) * jmax * jmax;
+    // the row walk reads the box a row at a time: ask L2 for all of it now
+    // (addresses inside the box only; a prefetch is a hint and loads nothing)
+    {
+      const char* bp = reinterpret_cast<const char*>(box);
+      const int nbytes = Jw * Jw * static_cast<int>(sizeof(C));
+      for (int off = lane * 128; off < nbytes; off += 32 * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(bp + off));
+    }
     const int64_t gbase = static_cast<int64_t>(stack_slot[r.stack]) * npad * npad;
     const uint32_t pm = perm[i];
     const int64_t src = pm & 0x7fffffffu;
@@ -366,29 +376,35 @@ __global__ void __launch_bounds__(256) dde_conv_kernel(
       const int run = lane / nb, cu = c0 + lane - run * nb;
       const int r0 = run * len, r1 = min(Jc, r0 + len);
       if (run >= runs || r0 >= r1) continue;
-      C* ring_l = ring + lane;
-      int slot = max(0, r0 - 2 * h) % jd;
-      auto row_pass = [&](int kb) {
-        C acc = cmake<C>(0.0, 0.0);
-        for (int s = 0; s < jd; ++s) {
-          const int ka = cu - 2 * h + s;
-          if (ka >= 0 && ka < Jw) cmad(acc, dab[s], box[kb * Jw + ka]);
-        }
-        ring_l[slot * 32] = acc;
-        slot = slot + 1 == jd ? 0 : slot + 1;
-      };
-      for (int kb = max(0, r0 - 2 * h); kb < min(r0, Jw); ++kb) row_pass(kb);
+      // the row pass's taps of this column: box columns cu - 2 h + s, s in [s0, s1)
+      const int s0 = max(0, h2 - cu), s1 = min(jd, Jw + h2 - cu);
+      const int ka0 = cu - h2;   // box column of s = 0
+      const int64_t gcol = gbase + wrap_index(r.bu + cu - h - half + 1, npad);
+      int grow = wrap_index(r.bv + r0 - h - half + 1, npad);
+      // rows of R from max(0, r0 - 2 h) on; row kb sits in ring slot kb mod jd
+      int kb_next = max(0, r0 - h2);
+      int slot = kb_next % jd;
       for (int cv = r0; cv < r1; ++cv) {
-        if (cv < Jw) row_pass(cv);
-        const int lo = max(0, cv - 2 * h), hi = min(Jw - 1, cv);
+        for (; kb_next <= min(cv, Jw - 1); ++kb_next) {
+          C acc = cmake<C>(0.0, 0.0);
+          const int k0 = kb_next * Jw + ka0;   // k0 + s >= kb_next * Jw for s >= s0
+          for (int s = s0; s < s1; ++s) cmad(acc, dab[s], box[k0 + s]);
+          ring_l[slot * 32] = acc;
+          slot = slot + 1 == jd ? 0 : slot + 1;
+        }
+        // rows kb = cv - 2 h .. cv of R inside the box, b index kb - cv + 2 h
+        const int lo = max(0, cv - h2), hi = min(Jw - 1, cv);
         C acc = cmake<C>(0.0, 0.0);
-        for (int kb = lo, sl = lo % jd; kb <= hi; ++kb, sl = sl + 1 == jd ? 0 : sl + 1)
-          cmad(acc, dab[jd + kb - cv + 2 * h], ring_l[sl * 32]);
+        int sl = slot - (hi - lo + 1);
+        if (sl < 0) sl += jd;
+        for (int kb = lo, jb = lo - cv + h2; kb <= hi; ++kb, ++jb) {
+          cmad(acc, dbv[jb], ring_l[sl * 32]);
+          sl = sl + 1 == jd ? 0 : sl + 1;
+        }
         ++my_taps;
-        const int ou = cu - h - half + 1, ov = cv - h - half + 1;
-        const int64_t gi = gbase + static_cast<int64_t>(wrap_index(r.bv + ov, npad)) * npad +
-                           wrap_index(r.bu + ou, npad);
-        apply_tap<C, kGrid>(acc, gi, yv, grid_in, grid_out, fx, accv);
+        apply_tap<C, kGrid>(acc, gcol + static_cast<int64_t>(grow) * npad, yv, grid_in, grid_out,
+                            fx, accv);
+        grow = grow + 1 == npad ? 0 : grow + 1;
       }
     }
     // the DDE taps and the ring are rewritten for the next visibility
